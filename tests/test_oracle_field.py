@@ -1,0 +1,100 @@
+"""Pins of the oracle's field-level step (streaming + collision on a periodic grid).
+
+Checks: streaming moves every population along its own velocity (Eq. advection);
+a uniform state is a fixed point; mass and momentum are conserved to round-off
+and streaming preserves the global H (Sec. I); the collision obeys the H theorem
+node by node with alpha_H (Sec. III); and the low-Re Taylor-Green vortex decays
+at the rate set by nu = theta (1/beta - 1)/2 (Sec. I: beta = dt/(2 tau + dt),
+nu = tau theta).  Citations are to arXiv:2203.12946.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2203_12946_gb300 import inputs
+
+
+@pytest.mark.parametrize("D,dims", [(2, (7, 5, 1)), (3, (5, 4, 3))])
+def test_stream_moves_along_velocity(D, dims):
+    """f_i(x + c_i, t + 1) = f*_i(x, t) with periodic wrap."""
+    c, _ = O.lattice(D)
+    Q = 3 ** D
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    rng = np.random.default_rng(5)
+    f = rng.random((Q, N))
+    g = O.stream(D, dims, f)
+    X, Y, Z = inputs.grid(dims)
+    for i in range(Q):
+        dst = ((Z + (c[i, 2] if D == 3 else 0)) % nz * ny + (Y + c[i, 1]) % ny) * nx + (X + c[i, 0]) % nx
+        assert np.array_equal(g[i, dst], f[i, np.arange(N)])
+
+
+@pytest.mark.parametrize("D,dims", [(2, (6, 4, 1)), (3, (3, 4, 5))])
+def test_uniform_state_is_fixed_point(D, dims):
+    N = int(np.prod(dims))
+    u = np.array([0.04, -0.03, 0.02][:D])
+    f0 = O.init_equilibrium(D, np.full(N, 1.1), np.repeat(u[:, None], N, axis=1))
+    f1, alpha, br, _ = O.step(D, dims, f0, 0.97, want_alpha=True)
+    assert np.max(np.abs(f1 - f0)) < 1e-16
+    assert np.all(alpha == 2.0) and np.all(br == O.BRANCH_CUTOFF)
+
+
+@pytest.mark.parametrize("D,dims", [(2, (24, 20, 1)), (3, (10, 9, 8))])
+def test_conservation_and_H_theorem_on_fields(D, dims):
+    """Global mass and momentum are conserved to round-off, and with alpha_H every node's
+    collision has H[f*] - H[f] <= 0, so the global H never grows (cutoff disabled)."""
+    rng = np.random.default_rng(7)
+    N = int(np.prod(dims))
+    rho = 1.0 + 0.02 * (2 * rng.random(N) - 1)
+    u = 0.05 * rng.standard_normal((D, N))
+    f = O.init_equilibrium(D, rho, u)
+    c, _ = O.lattice(D)
+    mass0 = f.sum()
+    mom0 = (c.T @ f).sum(axis=1)
+    H_prev = O.H_total(D, f)
+    for s in range(6):
+        f, alpha, br, dH = O.step(D, dims, f, 0.995, cutoff=False, want_alpha=True, want_dH=True)
+        assert abs(f.sum() - mass0) < 1e-12 * mass0
+        assert np.max(np.abs((c.T @ f).sum(axis=1) - mom0)) < 1e-12 * mass0
+        assert np.all(dH <= 1e-15)
+        H = O.H_total(D, f)
+        assert H <= H_prev + 1e-12
+        H_prev = H
+        assert np.all(np.isfinite(alpha)) and np.all(f > 0)
+        # streaming alone leaves the global H unchanged (Sec. I)
+        assert abs(O.H_total(D, O.stream(D, dims, f)) - H) < 1e-12 * abs(H)
+
+
+def test_taylor_green_decay_rate():
+    """D2Q9 64^2 Taylor-Green vortex, u0 = 0.01, beta = 0.9, 1000 steps (FP64): the kinetic
+    energy decays as exp(-4 nu k^2 t), k = 2 pi/64, nu = (1/3)(1/beta - 1)/2; fitted rate
+    within 1% (the paper gives no tolerance; O(Ma^2) and O(dx^2) errors are far smaller)."""
+    L, beta, u0 = 64, 0.9, 0.01
+    X, Y, _ = inputs.grid((L, L, 1))
+    rho, u = inputs.taylor_green_2d(X, Y, L, u0=u0)
+    f = O.init_equilibrium(2, rho, u)
+    ts, ke = [], []
+    t = 0
+    for chunk in range(10):
+        f, *_ = O.step(2, (L, L, 1), f, beta, nsteps=100)
+        t += 100
+        r, uu = O.moments_field(2, f)
+        ts.append(t)
+        ke.append(0.5 * np.sum(r * (uu ** 2).sum(axis=0)))
+    slope = np.polyfit(ts, np.log(ke), 1)[0]
+    nu = (1.0 / 3.0) * (1.0 / beta - 1.0) / 2.0
+    k = 2 * np.pi / L
+    expected = -4 * nu * k * k
+    assert abs(slope / expected - 1) < 0.01
+
+
+def test_step_threads_agree():
+    """The OpenMP split over z-slabs does not change the result."""
+    rng = np.random.default_rng(9)
+    dims = (9, 7, 6)
+    N = int(np.prod(dims))
+    f = O.init_equilibrium(3, 1 + 0.01 * rng.random(N), 0.04 * rng.standard_normal((3, N)))
+    a, *_ = O.step(3, dims, f, 0.99, nsteps=3, nthreads=1)
+    b, *_ = O.step(3, dims, f, 0.99, nsteps=3, nthreads=4)
+    assert np.array_equal(a, b)
