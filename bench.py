@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the essentially entropic lattice Boltzmann step on GB300.
+
+Workload: D3Q27, 256^3 periodic Taylor-Green vortex (u0 = 0.05, beta = 0.999),
+FP32 structure-of-arrays populations in ping-pong buffers; one "step" is one
+time step of the whole hot path (the fused pull-stream + collide kernel) plus,
+every 100 steps, the FP64 diagnostics pass (mass, momentum, H, alpha statistics,
+per-node H[f*] - H[f]).  Metric: MLUPS (million lattice-node updates per
+second), and the fused kernel's fraction of the measured HBM bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed.run as independent replicas (one full
+domain per GPU; the domain is not split across GPUs) and reports the aggregate.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L = 256
+BETA = 0.999
+U0 = 0.05
+LATTICE_Q = 27
+DIAG_EVERY = 100
+STORAGE = "f32"
+BYTES_PER_NODE = 2 * LATTICE_Q * 4  # read Q + write Q FP32 populations
+WORKLOAD = "D3Q27 256^3 periodic Taylor-Green vortex, u0=0.05, beta=0.999, FP32 SoA ping-pong"
+METRIC = "MLUPS (D3Q27 256^3 FP32 entropic LBM step)"
+PROFILE = os.path.join(ROOT, "profiles", "k_step_d3q27_f32_tgv256.md")
+KERNEL_SOURCES = ["paper_2203_12946_gb300/csrc/elbm_device.cuh",
+                  "paper_2203_12946_gb300/csrc/elbm_kernels.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_bytes = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not (m_hash and m_bytes) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd.insert(1, f"--id={self.uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+
+def oracle_prepare(slab: int):
+    """A 256 x 256 x slab periodic slab of the 256^3 Taylor-Green field as oracle populations
+    (same per-node work as the full domain)."""
+    import oracle as O
+    from paper_2203_12946_gb300 import inputs
+
+    dims = (L, L, slab)
+    X, Y, Z = inputs.grid(dims)
+    rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=U0)
+    return dims, O.init_equilibrium(3, rho, u)
+
+
+def oracle_time(dims, f, nsteps: int, nthreads: int = 0):
+    """Times nsteps oracle steps; returns (MLUPS, threads, seconds, description)."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    O.step(3, dims, f, BETA, nsteps=nsteps, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    n = f.shape[1] * nsteps
+    desc = (f"FP64 C oracle, {nsteps} step(s) of a 256x256x{dims[2]} periodic slab of the 256^3 "
+            f"Taylor-Green field ({n} node updates)")
+    return n / dt / 1e6, O.max_threads() if nthreads <= 0 else nthreads, dt, desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    O.build()
+    threads = O.max_threads()
+    # size the per-step sample so that warm-up + timed steps take about a minute
+    probe_rate, _, _, _ = oracle_time(*oracle_prepare(2), 1)
+    budget_nodes = probe_rate * 1e6 * 60.0 / max(1, args.steps + args.warmup)
+    slab = int(max(1, min(L, budget_nodes // (L * L))))
+    dims, f = oracle_prepare(slab)
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_time(dims, f, 1)
+    total = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        _, _, dt, desc = oracle_time(dims, f, 1)
+        total += dt
+    value = L * L * slab * args.steps / total / 1e6
+    wall = time.perf_counter() - t0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"each step: one step of a 256x256x{slab} slab"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    from paper_2203_12946_gb300 import elbm as E
+    from paper_2203_12946_gb300 import inputs
+
+    world, rank, local = dist_env()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    E.load()
+
+    dims = (L, L, L)
+    N = L ** 3
+    X, Y, Z = inputs.grid(dims)
+    rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=U0)
+    del X, Y, Z
+    # pinned host copies for the end-to-end leg
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+    rho_d = rho_h.to(dev)
+    u_d = u_h.to(dev)
+
+    stream = torch.cuda.current_stream(dev)
+    sim = E.Simulation(E.ELBM_D3Q27, dims, BETA, storage=STORAGE, device=local, stream=stream)
+    sim.init_equilibrium(rho_d, u_d)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def one_step(k, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        sim.step(1)
+        if ev is not None:
+            ev[1].record(stream)
+        if (k + 1) % DIAG_EVERY == 0:
+            E.elbm_diagnostics(sim.h)  # synchronising FP64 reduction pass (row a11)
+
+    for k in range(args.warmup):
+        one_step(k)
+    barrier()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    start.record(stream)
+    for k in range(args.steps):
+        one_step(k, evs[k])
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed = start.elapsed_time(stop) / 1e3
+    kern = [a.elapsed_time(b) / 1e3 for a, b in evs]
+    kern_avg = float(np.mean(kern))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    gpu_launches = args.steps + args.steps // DIAG_EVERY
+    d = sim.diagnostics()
+
+    # End to end through the C ABI with host buffers: initial rho/u uploaded from pinned
+    # host memory, K steps (with the diagnostics cadence), rho/u read back to host.
+    rho_out = torch.empty(N, dtype=torch.float64).pin_memory()
+    u_out = torch.empty((3, N), dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    E.elbm_init_equilibrium(sim.h, rho_h.numpy(), u_h.numpy(), E.ELBM_MEM_HOST)
+    for k in range(args.steps):
+        one_step(k)
+    E.elbm_moments(sim.h, rho_out.numpy(), u_out.numpy(), E.ELBM_MEM_HOST)
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    h2d = (rho_h.numel() + u_h.numel()) * 8
+    d2h = (rho_out.numel() + u_out.numel()) * 8
+
+    peak, peak_src = measured_peaks()
+    achieved = BYTES_PER_NODE * N / kern_avg / 1e9
+    traffic = profiled_traffic()
+    value = world * N * args.steps / elapsed / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "D3Q27", "dims": [L, L, L], "beta": BETA,
+                   "u0": U0, "storage": STORAGE, "diag_every": DIAG_EVERY,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (two 1.81 GB population buffers)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "k_step<StoreF32> (D3Q27)",
+                     "algorithmic_bytes_per_launch": BYTES_PER_NODE * N,
+                     "kernel_ms_avg": 1e3 * kern_avg},
+        "e2e": {"value": world * N * args.steps / e2e_t / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "what": "elbm_init_equilibrium from pinned host rho,u + K steps + elbm_moments to host"},
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "physics": {"alpha_min": d["alpha_min"], "alpha_max": d["alpha_max"],
+                    "n_solved_frac": d["n_solved"] / N, "n_clamped": d["n_clamped"],
+                    "n_nonpositive": d["n_nonpositive"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, threads, dt, desc = oracle_time(*oracle_prepare(args.cpu_slab), args.cpu_steps)
+        line["cpu_baseline"] = {"value": rate, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-slab", type=int, default=32)
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * elbm.h -- C ABI of the GB300 library for the essentially entropic lattice
+ * Boltzmann step of Atif, Kolluru & Ansumali, "Essentially entropic lattice
+ * Boltzmann model: Theory and simulations" (arXiv:2203.12946).
+ *
+ * One time step, per lattice node (Sec. I, Sec. III, Appendix D):
+ *   1. pull-stream the Q populations from the neighbours (Eq. advection),
+ *   2. form rho and u (Sec. I) and the product-form entropic equilibrium,
+ *   3. x_i = f_i^eq / f_i - 1 (Eq. xdef),
+ *   4. the closed-form path length alpha: alpha = 2 when |x|max < 1e-3,
+ *      otherwise alpha_Lower (Eq. alphaLowerSoln), the upper bound h (Eq.
+ *      gaplhah0) and alpha_Higher (Eq. qaud_tight, qaud_tight_coeff), then the
+ *      positivity clamp (Appendix D),
+ *   5. relax f* = f + alpha beta (f^eq - f) (Eq. fstar_def) and store.
+ *
+ * Conventions shared by every entry point
+ *  - All functions return an int status (ELBM_OK or a negative ELBM_ERR_*).
+ *    No exception, abort or exit crosses the ABI.  A failed call leaves a
+ *    message in elbm_last_error(handle) (or elbm_last_error(NULL) when no
+ *    handle exists yet).
+ *  - Lattices: D2Q9 and D3Q27, the tensor products of D1Q3 (Sec. I).
+ *    Velocity i enumerates (c_x, c_y[, c_z]) in {-1,0,1}^D lexicographically
+ *    with the last axis fastest: i = sum_a (c_a + 1) 3^(D-1-a); the opposite
+ *    velocity of i is Q-1-i.  Weights are products of the D1Q3 weights
+ *    {1/6, 4/6, 1/6}.
+ *  - Populations are stored structure-of-arrays: element (i, n) at offset
+ *    i*N + n, with node index n = (z*ny + y)*nx + x, N = nx*ny*nz (nz = 1 for
+ *    D2Q9).  The element type is the storage type of the handle (see
+ *    ELBM_STORE_*).  The stored state is the post-collision field f*.
+ *  - Macroscopic arrays are IEEE double: rho[n] (N values) and u[a*N + n]
+ *    (D x N values).
+ *  - Asynchrony: entry points enqueue work on the handle's CUDA stream.
+ *    Functions that return data to the host (elbm_diagnostics, elbm_moments
+ *    and elbm_alpha_field with host outputs, elbm_get_populations with a host
+ *    destination) synchronise that stream; a device fault raised by earlier
+ *    asynchronous work is reported by the next synchronising call as
+ *    ELBM_ERR_CUDA.
+ *  - Boundary conditions: periodic only (the paper's wall condition is cited,
+ *    not specified).
+ */
+#ifndef ELBM_H_
+#define ELBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define ELBM_OK 0
+#define ELBM_ERR_ARG (-1)         /* invalid argument (lattice, dims, beta, null pointer, size) */
+#define ELBM_ERR_UNSUPPORTED (-2) /* valid but not implemented (boundary condition, option)   */
+#define ELBM_ERR_CUDA (-3)        /* a CUDA call failed; see elbm_last_error                  */
+#define ELBM_ERR_NONPHYSICAL (-4) /* a population is <= 0 or not finite (positivity polytope) */
+#define ELBM_ERR_TIMEOUT (-5)     /* a bounded device-side wait expired                       */
+
+/* Lattices (value = Q). */
+#define ELBM_D2Q9 9
+#define ELBM_D3Q27 27
+
+/* Boundary conditions. */
+#define ELBM_BC_PERIODIC 0
+
+/* Storage of the populations.  F64 and F32 store f_i and compute in the same
+ * precision.  F16DEV and BF16DEV store the deviation f_i - w_i rho0 in IEEE
+ * half or bfloat16 and compute in FP32. */
+#define ELBM_STORE_F64 0
+#define ELBM_STORE_F32 1
+#define ELBM_STORE_F16DEV 2
+#define ELBM_STORE_BF16DEV 3
+
+/* Path-length rule.  HIGHER is the paper's alpha_Higher (default); LOWER the
+ * more dissipative alpha_Lower (Sec. III A); LBGK the constant alpha = 2. */
+#define ELBM_ALPHA_HIGHER 0
+#define ELBM_ALPHA_LOWER 1
+#define ELBM_ALPHA_LBGK 2
+
+/* Reading of the Omega+ denominators in the b coefficient (Eq.
+ * qaud_tight_coeff): DERIVED uses 4 + m alpha_Lower beta x (m = 1, 2, 3), as
+ * the lower-bound split of Appendix C gives; PRINTED uses 4 + m alpha_Lower x
+ * as typeset. */
+#define ELBM_B_DERIVED 0
+#define ELBM_B_PRINTED 1
+
+/* Location of a caller buffer. */
+#define ELBM_MEM_DEVICE 0
+#define ELBM_MEM_HOST 1
+
+/* Per-node flags written by elbm_alpha_field. */
+#define ELBM_BRANCH_CUTOFF 0  /* alpha = 2 (|x|max < 1e-3, or x == 0, or LBGK) */
+#define ELBM_BRANCH_SOLVED 1  /* alpha from the closed form                   */
+#define ELBM_BRANCH_CLAMPED 2 /* alpha reduced by the positivity clamp        */
+
+/* Number of interior bins of the alpha histogram (on [1.9, 2.1)); the
+ * histogram array has ELBM_HIST_BINS + 2 entries: [0] counts alpha < 1.9,
+ * [ELBM_HIST_BINS + 1] counts alpha >= 2.1. */
+#define ELBM_HIST_BINS 256
+
+typedef struct elbm_opts {
+    int storage;    /* ELBM_STORE_*, default ELBM_STORE_F32                          */
+    int alpha_mode; /* ELBM_ALPHA_*, default ELBM_ALPHA_HIGHER                       */
+    int cutoff;     /* 1: alpha = 2 when |x|max < 1e-3 (Appendix D, default); 0: off */
+    int b_variant;  /* ELBM_B_*, default ELBM_B_DERIVED                              */
+    int device;     /* CUDA device ordinal, default 0                                */
+    double rho0;    /* reference density of deviation storage, default 1.0           */
+    void *stream;   /* cudaStream_t for all work; NULL = the legacy default stream   */
+} elbm_opts;
+
+/* Domain-wide diagnostics of the current state and of the collision that the
+ * next step will apply (Eq. hdef, Eq. deltaH3), accumulated in FP64. */
+typedef struct elbm_diag {
+    double mass;        /* sum over nodes of rho                                      */
+    double momentum[3]; /* sum over nodes of rho u (zero beyond D)                        */
+    double H;           /* sum over nodes of H[f] = <f, log(f/w) - 1> (streamed state)    */
+    double dH_max;      /* max over nodes of H[f*] - H[f] of the next collision           */
+    double alpha_min;   /* min / max / mean over nodes of the next collision's alpha      */
+    double alpha_max;
+    double alpha_mean;
+    int64_t n_nodes;
+    int64_t n_cutoff;      /* nodes on the alpha = 2 branch                             */
+    int64_t n_solved;      /* nodes with the closed-form alpha                          */
+    int64_t n_clamped;     /* nodes where the positivity clamp acted                    */
+    int64_t n_nonpositive; /* nodes with a population <= 0 or not finite                */
+    int64_t n_dH_positive; /* nodes with H[f*] - H[f] > 1e-6 <f, x^2> (an H-theorem
+                              violation beyond the rounding of alpha)                   */
+} elbm_diag;
+
+typedef struct elbm elbm_t;
+
+/* Fills *opts with the defaults listed in elbm_opts. */
+void elbm_default_opts(elbm_opts *opts);
+
+/* Bytes of ONE population buffer (Q * N * sizeof(storage element)) for the
+ * given lattice, dims and storage.  Returns ELBM_ERR_ARG on invalid input. */
+int elbm_population_bytes(int lattice, const int64_t dims[3], int storage, size_t *bytes);
+
+/* Creates a handle for a periodic lattice of dims = {nx, ny, nz} nodes (nz = 1
+ * for D2Q9) with relaxation parameter beta = dt/(2 tau + dt), 0 < beta < 1
+ * (Sec. I).  opts may be NULL (defaults).  No device memory is allocated for
+ * the populations until elbm_bind_buffers or the first call that needs them;
+ * a small device scratch block for the diagnostics reductions is allocated
+ * here.  Errors: ELBM_ERR_ARG (null out, lattice not 9/27, any dim < 1, nz != 1
+ * for D2Q9, beta outside (0,1), rho0 <= 0, unknown storage/mode/variant),
+ * ELBM_ERR_UNSUPPORTED (bc != ELBM_BC_PERIODIC), ELBM_ERR_CUDA. */
+int elbm_create(elbm_t **out, int lattice, const int64_t dims[3], double beta, int bc,
+                const elbm_opts *opts);
+
+/* Frees the handle and every buffer the library allocated.  Borrowed buffers
+ * are not freed.  Safe on NULL. */
+void elbm_destroy(elbm_t *h);
+
+/* Message of the last failed call on h (or of the last failed elbm_create when
+ * h is NULL).  The string is owned by the library and valid until the next
+ * call on the same handle. */
+const char *elbm_last_error(const elbm_t *h);
+
+/* Binds two caller-owned device buffers of at least elbm_population_bytes
+ * bytes each, 256-byte aligned (ping-pong pair: each step reads one and writes
+ * the other).  The library never frees them; they must outlive the handle or
+ * the next bind.  Any buffers the library had allocated are freed.  The
+ * contents become the state: call elbm_init_equilibrium or
+ * elbm_set_populations before stepping.  Errors: ELBM_ERR_ARG (null, aliasing,
+ * too small, misaligned). */
+int elbm_bind_buffers(elbm_t *h, void *pop_a, void *pop_b, size_t bytes);
+
+/* Sets the stream used by all later work of h (NULL = legacy default stream). */
+int elbm_set_stream(elbm_t *h, void *stream);
+
+/* Initial state f = f^eq(rho, u) at every node (Sec. I equilibrium), computed
+ * in FP64 and rounded to the storage type.  rho: N doubles (NULL = uniform
+ * rho0); u: D*N doubles, u[a*N + n].  where = ELBM_MEM_DEVICE or ELBM_MEM_HOST
+ * (host arrays are copied through a library-owned staging buffer).  Resets
+ * the step counter.  Errors: ELBM_ERR_ARG (u NULL, bad where), ELBM_ERR_CUDA. */
+int elbm_init_equilibrium(elbm_t *h, const double *rho, const double *u, int where);
+
+/* Advances the state by n >= 0 time steps (one fused pull-stream + collide
+ * kernel launch per step, ping-pong between the two buffers).  Asynchronous.
+ * Errors: ELBM_ERR_ARG (n < 0), ELBM_ERR_CUDA (launch failure). */
+int elbm_step(elbm_t *h, int64_t n);
+
+/* rho and u of the current (post-collision) state at every node, computed in
+ * FP64 from the stored populations.  rho_out: N doubles (may be NULL); u_out:
+ * D*N doubles (may be NULL).  Host outputs synchronise the stream. */
+int elbm_moments(elbm_t *h, double *rho_out, double *u_out, int where);
+
+/* Per-node path length that the NEXT collision will apply (the current state
+ * is pull-streamed and alpha evaluated exactly as elbm_step does, in the
+ * storage's compute precision; nothing is written back).  alpha_out: N
+ * doubles; flags_out: N bytes of ELBM_BRANCH_* (may be NULL).  Both in the
+ * same memory space (where).  Host outputs synchronise the stream. */
+int elbm_alpha_field(elbm_t *h, double *alpha_out, uint8_t *flags_out, int where);
+
+/* Domain-wide diagnostics: mass, momentum and H of the current state, and the
+ * alpha statistics, per-node entropy change H[f*] - H[f] (Eq. deltaH3, FP64)
+ * and branch counts of the next collision.  alpha_hist (host, may be NULL)
+ * receives ELBM_HIST_BINS + 2 counts.  Synchronises the stream.  Returns
+ * ELBM_ERR_NONPHYSICAL (after filling *out) when any node has a population
+ * <= 0 or not finite. */
+int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist);
+
+/* Copies the current population buffer (Q*N storage elements, layout above)
+ * to dst / from src.  where selects host or device memory.  Host copies
+ * synchronise the stream.  set resets the step counter. */
+int elbm_get_populations(elbm_t *h, void *dst, int where);
+int elbm_set_populations(elbm_t *h, const void *src, int where);
+
+/* Steps taken since the last init/set. */
+int elbm_step_count(const elbm_t *h, int64_t *steps);
+
+/* Waits for all work enqueued on the handle's stream; reports deferred
+ * device errors as ELBM_ERR_CUDA. */
+int elbm_synchronize(elbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELBM_H_ */

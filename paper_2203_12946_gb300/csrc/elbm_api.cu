@@ -1,0 +1,505 @@
+// elbm_api.cu -- the C ABI declared in include/elbm.h: argument validation,
+// buffer ownership, stream handling and kernel dispatch.  All arithmetic of the
+// step lives in the kernels (elbm_kernels.cuh); this file only marshals.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "elbm.h"
+#include "elbm_device.cuh"
+#include "elbm_launch.h"
+
+using eelbm::CollideParams;
+using eelbm::DiagAcc;
+using eelbm::Geometry;
+
+struct elbm {
+    int lattice = 0, D = 0, Q = 0;
+    Geometry g{};
+    double beta = 0.0;
+    elbm_opts opts{};
+    cudaStream_t stream = nullptr;
+    void *pop[2] = {nullptr, nullptr};
+    bool owned = false; // library allocated pop[]
+    size_t pop_bytes = 0;
+    int cur = 0; // buffer holding the current state
+    double *stage = nullptr;
+    size_t stage_bytes = 0;
+    DiagAcc *acc = nullptr;
+    int num_sms = 0;
+    int64_t steps = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(elbm_t *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(elbm_t *h, cudaError_t e, const char *what)
+{
+    return fail(h, ELBM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+size_t storage_size(int storage)
+{
+    switch (storage) {
+    case ELBM_STORE_F64: return 8;
+    case ELBM_STORE_F32: return 4;
+    case ELBM_STORE_F16DEV:
+    case ELBM_STORE_BF16DEV: return 2;
+    default: return 0;
+    }
+}
+
+CollideParams params_of(const elbm_t *h)
+{
+    CollideParams p;
+    p.beta = h->beta;
+    p.mode = h->opts.alpha_mode;
+    p.cutoff = h->opts.cutoff;
+    p.b_variant = h->opts.b_variant;
+    p.rho0 = h->opts.rho0;
+    return p;
+}
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t status = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        status = cudaGetDevice(&prev);
+        if (status == cudaSuccess && prev != dev) status = cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+int ensure_populations(elbm_t *h)
+{
+    if (h->pop[0]) return ELBM_OK;
+    void *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaMalloc(&a, h->pop_bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(populations)");
+    e = cudaMalloc(&b, h->pop_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        return cuda_fail(h, e, "cudaMalloc(populations)");
+    }
+    h->pop[0] = a;
+    h->pop[1] = b;
+    h->owned = true;
+    h->cur = 0;
+    return ELBM_OK;
+}
+
+int ensure_stage(elbm_t *h, size_t bytes)
+{
+    if (h->stage_bytes >= bytes) return ELBM_OK;
+    if (h->stage) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&h->stage), bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(staging)");
+    h->stage_bytes = bytes;
+    return ELBM_OK;
+}
+
+#define ELBM_BY_LATTICE(h, FN, ...)                                                               \
+    ((h)->D == 2 ? eelbm::FN##_d2q9(__VA_ARGS__) : eelbm::FN##_d3q27(__VA_ARGS__))
+
+} // namespace
+
+extern "C" {
+
+void elbm_default_opts(elbm_opts *o)
+{
+    if (!o) return;
+    o->storage = ELBM_STORE_F32;
+    o->alpha_mode = ELBM_ALPHA_HIGHER;
+    o->cutoff = 1;
+    o->b_variant = ELBM_B_DERIVED;
+    o->device = 0;
+    o->rho0 = 1.0;
+    o->stream = nullptr;
+}
+
+int elbm_population_bytes(int lattice, const int64_t dims[3], int storage, size_t *bytes)
+{
+    if (!dims || !bytes) return fail(nullptr, ELBM_ERR_ARG, "elbm_population_bytes: null argument");
+    if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_population_bytes: lattice must be 9 or 27");
+    const size_t es = storage_size(storage);
+    if (!es) return fail(nullptr, ELBM_ERR_ARG, "elbm_population_bytes: unknown storage %d", storage);
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(nullptr, ELBM_ERR_ARG, "elbm_population_bytes: dims[%d] = %lld out of range", a,
+                        (long long)dims[a]);
+    const unsigned __int128 n = (unsigned __int128)dims[0] * dims[1] * dims[2] * lattice * es;
+    if (n > (unsigned __int128)SIZE_MAX / 4)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_population_bytes: domain too large");
+    *bytes = size_t(n);
+    return ELBM_OK;
+}
+
+int elbm_create(elbm_t **out, int lattice, const int64_t dims[3], double beta, int bc,
+                const elbm_opts *opts)
+{
+    if (!out) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: dims is NULL");
+    if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: lattice must be ELBM_D2Q9 (9) or ELBM_D3Q27 (27), got %d",
+                    lattice);
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(nullptr, ELBM_ERR_ARG, "elbm_create: dims[%d] = %lld out of range", a, (long long)dims[a]);
+    if (lattice == ELBM_D2Q9 && dims[2] != 1)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: D2Q9 needs dims[2] == 1");
+    if (!(beta > 0.0 && beta < 1.0))
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: beta must lie in (0, 1), got %g", beta);
+    if (bc != ELBM_BC_PERIODIC)
+        return fail(nullptr, ELBM_ERR_UNSUPPORTED, "elbm_create: only periodic boundaries are supported");
+    elbm_opts o;
+    elbm_default_opts(&o);
+    if (opts) o = *opts;
+    if (!storage_size(o.storage)) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown storage %d", o.storage);
+    if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_LBGK)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown alpha_mode %d", o.alpha_mode);
+    if (o.b_variant != ELBM_B_DERIVED && o.b_variant != ELBM_B_PRINTED)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown b_variant %d", o.b_variant);
+    if (o.cutoff != 0 && o.cutoff != 1) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: cutoff must be 0 or 1");
+    if (!(o.rho0 > 0.0)) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: rho0 must be positive");
+    size_t bytes = 0;
+    int st = elbm_population_bytes(lattice, dims, o.storage, &bytes);
+    if (st != ELBM_OK) return st;
+    if (dims[0] * dims[1] * dims[2] > (int64_t(1) << 31))
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: more than 2^31 nodes");
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "elbm_create: cudaGetDeviceCount");
+    if (o.device < 0 || o.device >= ndev)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: device %d not present (%d devices)", o.device, ndev);
+    DeviceGuard guard(o.device);
+    if (guard.status != cudaSuccess) return cuda_fail(nullptr, guard.status, "elbm_create: cudaSetDevice");
+
+    elbm_t *h = new (std::nothrow) elbm_t();
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: out of host memory");
+    h->lattice = lattice;
+    h->D = lattice == ELBM_D2Q9 ? 2 : 3;
+    h->Q = lattice;
+    h->g.nx = int(dims[0]);
+    h->g.ny = int(dims[1]);
+    h->g.nz = int(dims[2]);
+    h->g.N = dims[0] * dims[1] * dims[2];
+    h->beta = beta;
+    h->opts = o;
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    h->pop_bytes = bytes;
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, o.device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(nullptr, e, "elbm_create: cudaDeviceGetAttribute");
+    }
+    e = cudaMalloc(reinterpret_cast<void **>(&h->acc), sizeof(DiagAcc));
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(nullptr, e, "elbm_create: cudaMalloc(diagnostics scratch)");
+    }
+    *out = h;
+    return ELBM_OK;
+}
+
+void elbm_destroy(elbm_t *h)
+{
+    if (!h) return;
+    DeviceGuard guard(h->opts.device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->owned) {
+        cudaFree(h->pop[0]);
+        cudaFree(h->pop[1]);
+    }
+    cudaFree(h->stage);
+    cudaFree(h->acc);
+    delete h;
+}
+
+const char *elbm_last_error(const elbm_t *h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int elbm_bind_buffers(elbm_t *h, void *pop_a, void *pop_b, size_t bytes)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_bind_buffers: handle is NULL");
+    if (!pop_a || !pop_b) return fail(h, ELBM_ERR_ARG, "elbm_bind_buffers: buffer is NULL");
+    if (pop_a == pop_b) return fail(h, ELBM_ERR_ARG, "elbm_bind_buffers: the two buffers alias");
+    if (bytes < h->pop_bytes)
+        return fail(h, ELBM_ERR_ARG, "elbm_bind_buffers: %zu bytes given, %zu needed", bytes, h->pop_bytes);
+    if ((reinterpret_cast<uintptr_t>(pop_a) | reinterpret_cast<uintptr_t>(pop_b)) & 255u)
+        return fail(h, ELBM_ERR_ARG, "elbm_bind_buffers: buffers must be 256-byte aligned");
+    const char *a = static_cast<const char *>(pop_a), *b = static_cast<const char *>(pop_b);
+    if (a < b + h->pop_bytes && b < a + h->pop_bytes)
+        return fail(h, ELBM_ERR_ARG, "elbm_bind_buffers: the two buffers overlap");
+    DeviceGuard guard(h->opts.device);
+    if (h->owned) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_bind_buffers: cudaStreamSynchronize");
+        cudaFree(h->pop[0]);
+        cudaFree(h->pop[1]);
+    }
+    h->pop[0] = pop_a;
+    h->pop[1] = pop_b;
+    h->owned = false;
+    h->cur = 0;
+    h->steps = 0;
+    return ELBM_OK;
+}
+
+int elbm_set_stream(elbm_t *h, void *stream)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_set_stream: handle is NULL");
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->opts.stream = stream;
+    return ELBM_OK;
+}
+
+int elbm_init_equilibrium(elbm_t *h, const double *rho, const double *u, int where)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_init_equilibrium: handle is NULL");
+    if (!u) return fail(h, ELBM_ERR_ARG, "elbm_init_equilibrium: u is NULL");
+    if (where != ELBM_MEM_DEVICE && where != ELBM_MEM_HOST)
+        return fail(h, ELBM_ERR_ARG, "elbm_init_equilibrium: bad memory location %d", where);
+    DeviceGuard guard(h->opts.device);
+    int st = ensure_populations(h);
+    if (st != ELBM_OK) return st;
+    const int64_t N = h->g.N;
+    const double *drho = rho, *du = u;
+    if (where == ELBM_MEM_HOST) {
+        const size_t need = size_t(N) * (1 + h->D) * sizeof(double);
+        if ((st = ensure_stage(h, need)) != ELBM_OK) return st;
+        double *srho = h->stage, *su = h->stage + N;
+        cudaError_t e;
+        if (rho) {
+            e = cudaMemcpyAsync(srho, rho, size_t(N) * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: copy rho");
+            drho = srho;
+        }
+        e = cudaMemcpyAsync(su, u, size_t(N) * h->D * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: copy u");
+        du = su;
+    }
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_init, h->opts.storage, drho, du, h->pop[0], h->g, h->opts.rho0,
+                                    h->opts.rho0, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: kernel launch");
+    if (where == ELBM_MEM_HOST) {
+        // the caller may reuse its host arrays as soon as we return
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: synchronize");
+    }
+    h->cur = 0;
+    h->steps = 0;
+    return ELBM_OK;
+}
+
+int elbm_step(elbm_t *h, int64_t n)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_step: handle is NULL");
+    if (n < 0) return fail(h, ELBM_ERR_ARG, "elbm_step: n = %lld < 0", (long long)n);
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_step: no state (call elbm_init_equilibrium first)");
+    DeviceGuard guard(h->opts.device);
+    const CollideParams p = params_of(h);
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = ELBM_BY_LATTICE(h, launch_step, h->opts.storage, h->pop[h->cur], h->pop[h->cur ^ 1], h->g, p,
+                                        h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_step: kernel launch");
+        h->cur ^= 1;
+        h->steps += 1;
+    }
+    return ELBM_OK;
+}
+
+int elbm_moments(elbm_t *h, double *rho_out, double *u_out, int where)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_moments: handle is NULL");
+    if (where != ELBM_MEM_DEVICE && where != ELBM_MEM_HOST)
+        return fail(h, ELBM_ERR_ARG, "elbm_moments: bad memory location %d", where);
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_moments: no state");
+    if (!rho_out && !u_out) return ELBM_OK;
+    DeviceGuard guard(h->opts.device);
+    const int64_t N = h->g.N;
+    double *drho = rho_out, *du = u_out;
+    int st;
+    if (where == ELBM_MEM_HOST) {
+        if ((st = ensure_stage(h, size_t(N) * (1 + h->D) * sizeof(double))) != ELBM_OK) return st;
+        drho = rho_out ? h->stage : nullptr;
+        du = u_out ? h->stage + N : nullptr;
+    }
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_moments, h->opts.storage, h->pop[h->cur], h->g, h->opts.rho0, drho,
+                                    du, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: kernel launch");
+    if (where == ELBM_MEM_HOST) {
+        if (rho_out) {
+            e = cudaMemcpyAsync(rho_out, drho, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: copy rho");
+        }
+        if (u_out) {
+            e = cudaMemcpyAsync(u_out, du, size_t(N) * h->D * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: copy u");
+        }
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: synchronize");
+    }
+    return ELBM_OK;
+}
+
+int elbm_alpha_field(elbm_t *h, double *alpha_out, uint8_t *flags_out, int where)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_alpha_field: handle is NULL");
+    if (!alpha_out) return fail(h, ELBM_ERR_ARG, "elbm_alpha_field: alpha_out is NULL");
+    if (where != ELBM_MEM_DEVICE && where != ELBM_MEM_HOST)
+        return fail(h, ELBM_ERR_ARG, "elbm_alpha_field: bad memory location %d", where);
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_alpha_field: no state");
+    DeviceGuard guard(h->opts.device);
+    const int64_t N = h->g.N;
+    double *da = alpha_out;
+    uint8_t *df = flags_out;
+    int st;
+    if (where == ELBM_MEM_HOST) {
+        if ((st = ensure_stage(h, size_t(N) * (sizeof(double) + 1) + 256)) != ELBM_OK) return st;
+        da = h->stage;
+        df = flags_out ? reinterpret_cast<uint8_t *>(h->stage + N) : nullptr;
+    }
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_alpha, h->opts.storage, h->pop[h->cur], h->g, params_of(h), da, df,
+                                    h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_alpha_field: kernel launch");
+    if (where == ELBM_MEM_HOST) {
+        e = cudaMemcpyAsync(alpha_out, da, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_alpha_field: copy alpha");
+        if (flags_out) {
+            e = cudaMemcpyAsync(flags_out, df, size_t(N), cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "elbm_alpha_field: copy flags");
+        }
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_alpha_field: synchronize");
+    }
+    return ELBM_OK;
+}
+
+int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_diagnostics: handle is NULL");
+    if (!out) return fail(h, ELBM_ERR_ARG, "elbm_diagnostics: out is NULL");
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_diagnostics: no state");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(DiagAcc), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&h->acc->amin_ord, 0xFF, sizeof(unsigned long long), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: clear scratch");
+    e = ELBM_BY_LATTICE(h, launch_diag, h->opts.storage, h->pop[h->cur], h->g, params_of(h), h->acc, h->num_sms,
+                        h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: kernel launch");
+    DiagAcc acc;
+    e = cudaMemcpyAsync(&acc, h->acc, sizeof acc, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: read back");
+    const int64_t N = h->g.N;
+    out->mass = acc.sum[0];
+    out->momentum[0] = acc.sum[1];
+    out->momentum[1] = acc.sum[2];
+    out->momentum[2] = h->D == 3 ? acc.sum[3] : 0.0;
+    out->H = acc.sum[4];
+    out->dH_max = eelbm::from_ordered_bits(acc.dH_max_ord);
+    out->alpha_min = eelbm::from_ordered_bits(acc.amin_ord);
+    out->alpha_max = eelbm::from_ordered_bits(acc.amax_ord);
+    out->alpha_mean = N ? acc.sum[5] / double(N) : 0.0;
+    out->n_nodes = N;
+    out->n_cutoff = int64_t(acc.cnt[0]);
+    out->n_solved = int64_t(acc.cnt[1]);
+    out->n_clamped = int64_t(acc.cnt[2]);
+    out->n_nonpositive = int64_t(acc.cnt[3]);
+    out->n_dH_positive = int64_t(acc.cnt[4]);
+    if (alpha_hist)
+        for (int b = 0; b < ELBM_HIST_BINS + 2; ++b) alpha_hist[b] = int64_t(acc.hist[b]);
+    if (out->n_nonpositive > 0)
+        return fail(h, ELBM_ERR_NONPHYSICAL, "elbm_diagnostics: %lld nodes with a population <= 0 or not finite",
+                    (long long)out->n_nonpositive);
+    return ELBM_OK;
+}
+
+int elbm_get_populations(elbm_t *h, void *dst, int where)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_get_populations: handle is NULL");
+    if (!dst) return fail(h, ELBM_ERR_ARG, "elbm_get_populations: dst is NULL");
+    if (where != ELBM_MEM_DEVICE && where != ELBM_MEM_HOST)
+        return fail(h, ELBM_ERR_ARG, "elbm_get_populations: bad memory location %d", where);
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_get_populations: no state");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = cudaMemcpyAsync(dst, h->pop[h->cur], h->pop_bytes,
+                                    where == ELBM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                    h->stream);
+    if (e == cudaSuccess && where == ELBM_MEM_HOST) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_get_populations");
+    return ELBM_OK;
+}
+
+int elbm_set_populations(elbm_t *h, const void *src, int where)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_set_populations: handle is NULL");
+    if (!src) return fail(h, ELBM_ERR_ARG, "elbm_set_populations: src is NULL");
+    if (where != ELBM_MEM_DEVICE && where != ELBM_MEM_HOST)
+        return fail(h, ELBM_ERR_ARG, "elbm_set_populations: bad memory location %d", where);
+    DeviceGuard guard(h->opts.device);
+    int st = ensure_populations(h);
+    if (st != ELBM_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h->pop[0], src, h->pop_bytes,
+                                    where == ELBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    h->stream);
+    if (e == cudaSuccess && where == ELBM_MEM_HOST) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_set_populations");
+    h->cur = 0;
+    h->steps = 0;
+    return ELBM_OK;
+}
+
+int elbm_step_count(const elbm_t *h, int64_t *steps)
+{
+    if (!h || !steps) return fail(nullptr, ELBM_ERR_ARG, "elbm_step_count: null argument");
+    *steps = h->steps;
+    return ELBM_OK;
+}
+
+int elbm_synchronize(elbm_t *h)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_synchronize: handle is NULL");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_synchronize");
+    return ELBM_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,311 @@
+// elbm_device.cuh -- device-side building blocks of the essentially entropic
+// lattice Boltzmann step (arXiv:2203.12946) for sm_103a.
+//
+// Contents
+//   * lattice constants of D2Q9 / D3Q27 as compile-time functions of the
+//     velocity index (tensor products of D1Q3, Sec. I);
+//   * storage traits (FP64, FP32, FP16/BF16 deviation storage);
+//   * node_collide: moments, product-form entropic equilibrium, departures x,
+//     the closed-form path length of Sec. III / Appendix C with the cutoff and
+//     positivity clamp of Appendix D, evaluated on registers;
+//   * FP64 helpers for the diagnostics (Eq. hdef, Eq. deltaH3).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eelbm {
+
+// ---------------------------------------------------------------------------
+// Lattice: velocity i enumerates (c_x, c_y[, c_z]) in {-1,0,1}^D with the last
+// axis fastest.  Weights are products of the D1Q3 weights {1/6, 4/6, 1/6}.
+// ---------------------------------------------------------------------------
+template <int D>
+struct Lattice {
+    static constexpr int Q = D == 2 ? 9 : 27;
+};
+
+__host__ __device__ constexpr int vel(int D, int i, int a)
+{
+    return (a == D - 1 ? i : (a == D - 2 ? i / 3 : i / 9)) % 3 - 1;
+}
+
+__host__ __device__ constexpr double weight(int D, int i)
+{
+    double w = 1.0;
+    for (int a = 0; a < D; ++a) w *= (vel(D, i, a) == 0 ? 4.0 / 6.0 : 1.0 / 6.0);
+    return w;
+}
+
+struct Geometry {
+    int nx, ny, nz;
+    int64_t N;
+};
+
+// Near-equilibrium cutoff of Appendix D (strict test |x|max < 1e-3).
+constexpr double kCutoff = 1e-3;
+
+enum { kModeHigher = 0, kModeLower = 1, kModeLBGK = 2 };
+enum { kBranchCutoff = 0, kBranchSolved = 1, kBranchClamped = 2 };
+
+struct CollideParams {
+    double beta;
+    int mode;      // kMode*
+    int cutoff;    // 1 = Appendix D shortcut on
+    int b_variant; // 0 = derived denominators (alpha_L beta x), 1 = printed (alpha_L x)
+    double rho0;   // reference density of deviation storage
+};
+
+// ---------------------------------------------------------------------------
+// Arithmetic helpers.  FP32 divisions on the hot path use the fast reciprocal
+// intrinsic (max error 2 ulp); FP64 uses IEEE division.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+
+// ---------------------------------------------------------------------------
+// Storage traits.  load/store convert between the stored element and the
+// compute type; deviation storage keeps f_i - w_i rho0.
+// ---------------------------------------------------------------------------
+struct StoreF64 {
+    using S = double;
+    using T = double;
+    __device__ static __forceinline__ T load(S s, T, T) { return s; }
+    __device__ static __forceinline__ S store(T f, T, T) { return f; }
+    __device__ static __forceinline__ double load64(S s, double, double) { return s; }
+    __device__ static __forceinline__ S store64(double f, double, double) { return f; }
+};
+struct StoreF32 {
+    using S = float;
+    using T = float;
+    __device__ static __forceinline__ T load(S s, T, T) { return s; }
+    __device__ static __forceinline__ S store(T f, T, T) { return f; }
+    __device__ static __forceinline__ double load64(S s, double, double) { return double(s); }
+    __device__ static __forceinline__ S store64(double f, double, double) { return float(f); }
+};
+struct StoreF16Dev {
+    using S = __half;
+    using T = float;
+    __device__ static __forceinline__ T load(S s, T w, T rho0) { return fmaf(w, rho0, __half2float(s)); }
+    __device__ static __forceinline__ S store(T f, T w, T rho0) { return __float2half_rn(fmaf(-w, rho0, f)); }
+    __device__ static __forceinline__ double load64(S s, double w, double rho0)
+    {
+        return w * rho0 + double(__half2float(s));
+    }
+    __device__ static __forceinline__ S store64(double f, double w, double rho0)
+    {
+        return __double2half(f - w * rho0);
+    }
+};
+struct StoreBF16Dev {
+    using S = __nv_bfloat16;
+    using T = float;
+    __device__ static __forceinline__ T load(S s, T w, T rho0) { return fmaf(w, rho0, __bfloat162float(s)); }
+    __device__ static __forceinline__ S store(T f, T w, T rho0) { return __float2bfloat16_rn(fmaf(-w, rho0, f)); }
+    __device__ static __forceinline__ double load64(S s, double w, double rho0)
+    {
+        return w * rho0 + double(__bfloat162float(s));
+    }
+    __device__ static __forceinline__ S store64(double f, double w, double rho0)
+    {
+        return __double2bfloat16(f - w * rho0);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Positive root of -alpha^2 a + alpha b - c in the conjugate form of Eq.
+// alphaLowerSoln, 2c / (b + sqrt(b^2 - 4ac)), evaluated with b factored out,
+// 2q / (1 + sqrt(1 - 4 p q)) with q = c/b, p = a/b, so that no power of the
+// O(x^2) coefficients can underflow in FP32.  Requires b > 0; a <= 0 <= c.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T quad_root(T a, T b, T c)
+{
+    const T q = div_(c, b);
+    const T p = div_(a, b);
+    return div_(T(2) * q, T(1) + sqrt_(T(1) - T(4) * p * q));
+}
+
+// ---------------------------------------------------------------------------
+// Per-node collision on registers.
+//   in : f[Q]  pre-collision populations
+//   out: f[Q]  post-collision populations f* = f + alpha beta (f^eq - f)
+//        x[Q]  departures x_i = f^eq_i / f_i - 1 (Eq. xdef)
+//        returns alpha; *branch receives kBranch*
+// The relaxation uses f^eq - f = x f, so only f and x stay live.
+// ---------------------------------------------------------------------------
+template <int D, class T, bool kRelax = true>
+__device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q],
+                                          const CollideParams &p, int *branch)
+{
+    constexpr int Q = Lattice<D>::Q;
+    const T beta = T(p.beta);
+
+    // Moments (Sec. I): rho = <f,1>, rho u = <f,c>.
+    T rho = T(0);
+    T j[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) j[a] = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            if (vel(D, i, a) == 1) j[a] += f[i];
+            if (vel(D, i, a) == -1) j[a] -= f[i];
+        }
+    }
+    const T irho = div_(T(1), rho);
+
+    // Product-form entropic equilibrium (Sec. I): per axis
+    // Upsilon = 2 - sqrt(1 + 3u^2), z = (2u + sqrt(1 + 3u^2)) / (1 - u); the
+    // factor of axis a for c = -1, 0, +1 is (1/6) Y / z, (4/6) Y, (1/6) Y z.
+    T phi[D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const T u = j[a] * irho;
+        const T s = sqrt_(T(1) + T(3) * u * u);
+        const T Y = T(2) - s;
+        const T num = T(2) * u + s;
+        const T den = T(1) - u;
+        phi[a][0] = div_(Y * den, T(6) * num);
+        phi[a][1] = Y * T(4.0 / 6.0);
+        phi[a][2] = div_(Y * num, T(6) * den);
+    }
+
+    // Departures x_i = (f^eq_i - f_i) / f_i and their extremes.
+    T xabs = T(0), xmin = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T feq = rho;
+#pragma unroll
+        for (int a = 0; a < D; ++a) feq *= phi[a][vel(D, i, a) + 1];
+        x[i] = div_(feq - f[i], f[i]);
+        xabs = fmax(xabs, fabs(x[i]));
+        xmin = fmin(xmin, x[i]);
+    }
+
+    T alpha = T(2);
+    int br = kBranchCutoff;
+    if (p.mode != kModeLBGK && !(p.cutoff && xabs < T(kCutoff))) {
+        // Eq. alphaLowerCoeffs and the x-only parts of Eq. qaud_tight_coeff:
+        //   b1 = <f, x^2/2>, c1 = <f, 2x^2/(2+x)>,
+        //   c  = <f, (60x^2 + 60x^3 + 11x^4)/(60 + 90x + 36x^2 + 3x^3)>,
+        //   S_k = <f, x^k>_{Omega-} (k = 3..6), so a1 = S3/2, a2 = beta^2 S3/6.
+        T b1 = T(0), c1 = T(0), c = T(0), S3 = T(0), S4 = T(0), S5 = T(0), S6 = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const T xi = x[i];
+            const T fx2 = f[i] * xi * xi;
+            b1 += fx2;
+            c1 += div_(fx2, T(2) + xi);
+            c += div_(fx2 * (T(60) + xi * (T(60) + T(11) * xi)),
+                      T(60) + xi * (T(90) + xi * (T(36) + T(3) * xi)));
+            if (xi < T(0)) {
+                const T fx3 = fx2 * xi;
+                S3 += fx3;
+                S4 += fx3 * xi;
+                S5 += fx3 * xi * xi;
+                S6 += fx3 * xi * xi * xi;
+            }
+        }
+        b1 *= T(0.5);
+        c1 *= T(2);
+        if (b1 > T(0)) {
+            // alpha_Lower (Eq. alphaLowerSoln).
+            const T aL = quad_root(T(0.5) * S3, b1, c1);
+            if (p.mode == kModeLower) {
+                alpha = aL;
+            } else {
+                // b of Eq. qaud_tight_coeff.  With t = k x the bracket
+                // 2/(4+t) + 1/(4+2t) + 2/(4+3t) equals the single rational
+                // (80 + 80t + 19t^2) / (64 + 96t + 44t^2 + 6t^3).
+                const T k = p.b_variant ? aL : aL * beta;
+                T bp = T(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const T xi = x[i];
+                    if (xi >= T(0)) {
+                        const T t = k * xi;
+                        bp += div_(f[i] * xi * xi * xi * (T(80) + t * (T(80) + T(19) * t)),
+                                   T(64) + t * (T(96) + t * (T(44) + T(6) * t)));
+                    }
+                }
+                const T b = b1 - T(2.0 / 15.0) * aL * beta * beta * bp;
+                // Upper bound h: positive root of Eq. gaplhah0, a2 = beta^2 <f,x^3/6>_-.
+                const T h = quad_root(beta * beta * S3 * T(1.0 / 6.0), b, c);
+                // a of Eq. qaud_tight_coeff from the power sums.
+                const T hb = h * beta;
+                const T a = beta * beta *
+                            (S3 * T(1.0 / 6.0) - hb * S4 * T(1.0 / 12.0) + hb * hb * S5 * T(1.0 / 20.0) -
+                             hb * hb * hb * S6 * T(1.0 / 5.0));
+                alpha = quad_root(a, b, c); // alpha_Higher
+            }
+            br = kBranchSolved;
+        }
+    }
+    if (p.mode != kModeLBGK && xmin < T(0) && alpha * beta * (-xmin) > T(1)) {
+        // Positivity (Appendix D): alpha_max = -1/(beta x_min); alpha > alpha_max
+        // becomes (1 + alpha_max)/2, and alpha_max/2 when that still exceeds it.
+        const T amax = div_(T(-1), beta * xmin);
+        alpha = T(0.5) * (T(1) + amax);
+        if (alpha > amax) alpha = T(0.5) * amax;
+        br = kBranchClamped;
+    }
+    if (kRelax) {
+        const T ab = alpha * beta;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = fma(ab * x[i], f[i], f[i]);
+    }
+    *branch = br;
+    return alpha;
+}
+
+// ---------------------------------------------------------------------------
+// Pull streaming (Eq. advection): population i at node (x, y, z) comes from
+// (x - c_ix, y - c_iy, z - c_iz) with periodic wrap.
+// ---------------------------------------------------------------------------
+template <int D, class ST>
+__device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin, const Geometry &g,
+                                          int x, int y, int z, typename ST::T rho0,
+                                          typename ST::T (&f)[Lattice<D>::Q])
+{
+    using T = typename ST::T;
+    constexpr int Q = Lattice<D>::Q;
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel(D, i, 0), cy = vel(D, i, 1);
+        const int cz = D == 3 ? vel(D, i, 2) : 0;
+        const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+        const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+        const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+        const int64_t src = ((int64_t)sz * g.ny + sy) * g.nx + sx;
+        f[i] = ST::load(__ldg(fin + (int64_t)i * g.N + src), T(weight(D, i)), rho0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 diagnostics helpers.
+// g(y) = (1+y) log(1+y) - y; near 0 the Taylor series
+// sum_{k>=2} (-1)^k y^k / (k(k-1)) avoids the cancellation of the direct form.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double g_entropy(double y)
+{
+    if (y <= -1.0) return 1.0;
+    if (fabs(y) < 0.1) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 20; k >= 2; --k) s = s * y + ((k % 2 == 0) ? 1.0 : -1.0) / double(k * (k - 1));
+        return s * y * y;
+    }
+    return (1.0 + y) * log1p(y) - y;
+}
+
+} // namespace eelbm

@@ -1,0 +1,368 @@
+// elbm_kernels.cuh -- kernels of the essentially entropic lattice Boltzmann
+// step and its companions, instantiated once per lattice by elbm_d2q9.cu and
+// elbm_d3q27.cu (include this file after defining ELBM_DIM and ELBM_SUFFIX).
+//
+//   k_step     fused pull-stream + collide + store (Eq. advection, Eq.
+//              fstar_def, path length of Sec. III / Appendix C-D), one node per
+//              thread, ping-pong buffers
+//   k_init     f = f^eq(rho, u) (Sec. I equilibrium, FP64, rounded to storage)
+//   k_moments  rho and u of the stored state (FP64)
+//   k_alpha    path length of the next collision (no write-back)
+//   k_diag     domain reductions: mass, momentum, H (Eq. hdef), alpha statistics
+//              and per-node H[f*] - H[f] (Eq. deltaH3) in FP64; warp shuffles,
+//              then shared memory, then one atomic per block and quantity
+#pragma once
+
+#include "elbm_device.cuh"
+#include "elbm_launch.h"
+
+namespace eelbm {
+namespace ELBM_SUFFIX {
+
+constexpr int D = ELBM_DIM;
+constexpr int Q = Lattice<D>::Q;
+constexpr int kStepBlock = D == 2 ? 256 : 128;
+constexpr int kAuxBlock = 256;
+
+__device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x, int &y, int &z)
+{
+    const int64_t t = n / g.nx;
+    x = int(n - t * g.nx);
+    z = int(t / g.ny);
+    y = int(t - (int64_t)z * g.ny);
+}
+
+template <class ST>
+__global__ void __launch_bounds__(kStepBlock) k_step(const typename ST::S *__restrict__ fin,
+                                                    typename ST::S *__restrict__ fout, Geometry g,
+                                                    CollideParams p)
+{
+    using T = typename ST::T;
+    const int64_t n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
+    if (n >= g.N) return;
+    int x, y, z;
+    node_coords(n, g, x, y, z);
+    T f[Q], xd[Q];
+    const T rho0 = T(p.rho0);
+    pull_load<D, ST>(fin, g, x, y, z, rho0, f);
+    int br;
+    node_collide<D, T, true>(f, xd, p, &br);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
+}
+
+// FP64 equilibrium from rho and u (same product form as node_collide).
+__device__ __forceinline__ void equilibrium64(double rho, const double (&u)[3], double (&feq)[Q])
+{
+    double phi[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double s = sqrt(1.0 + 3.0 * u[a] * u[a]);
+        const double Y = 2.0 - s;
+        const double num = 2.0 * u[a] + s, den = 1.0 - u[a];
+        phi[a][0] = Y * den / (6.0 * num);
+        phi[a][1] = Y * (4.0 / 6.0);
+        phi[a][2] = Y * num / (6.0 * den);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        double v = rho;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v *= phi[a][vel(D, i, a) + 1];
+        feq[i] = v;
+    }
+}
+
+template <class ST>
+__global__ void __launch_bounds__(kAuxBlock) k_init(const double *__restrict__ rho,
+                                                   const double *__restrict__ u,
+                                                   typename ST::S *__restrict__ f, Geometry g,
+                                                   double rho_uniform, double rho0)
+{
+    const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+    if (n >= g.N) return;
+    double un[3] = {0.0, 0.0, 0.0}, feq[Q];
+#pragma unroll
+    for (int a = 0; a < D; ++a) un[a] = u[(int64_t)a * g.N + n];
+    equilibrium64(rho ? rho[n] : rho_uniform, un, feq);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[(int64_t)i * g.N + n] = ST::store64(feq[i], weight(D, i), rho0);
+}
+
+template <class ST>
+__global__ void __launch_bounds__(kAuxBlock) k_moments(const typename ST::S *__restrict__ f,
+                                                      Geometry g, double rho0,
+                                                      double *__restrict__ rho_out,
+                                                      double *__restrict__ u_out)
+{
+    const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+    if (n >= g.N) return;
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double v = ST::load64(f[(int64_t)i * g.N + n], weight(D, i), rho0);
+        r += v;
+#pragma unroll
+        for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * v;
+    }
+    if (rho_out) rho_out[n] = r;
+    if (u_out) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) u_out[(int64_t)a * g.N + n] = j[a] / r;
+    }
+}
+
+template <class ST>
+__global__ void __launch_bounds__(kStepBlock) k_alpha(const typename ST::S *__restrict__ fin,
+                                                     Geometry g, CollideParams p,
+                                                     double *__restrict__ alpha_out,
+                                                     uint8_t *__restrict__ flags)
+{
+    using T = typename ST::T;
+    const int64_t n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
+    if (n >= g.N) return;
+    int x, y, z;
+    node_coords(n, g, x, y, z);
+    T f[Q], xd[Q];
+    pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
+    int br;
+    const T alpha = node_collide<D, T, false>(f, xd, p, &br);
+    alpha_out[n] = double(alpha);
+    if (flags) flags[n] = uint8_t(br);
+}
+
+// --------------------------------------------------------------------------
+// Diagnostics reduction.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_min(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+template <class ST>
+__global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__restrict__ fin,
+                                                   Geometry g, CollideParams p,
+                                                   DiagAcc *__restrict__ acc)
+{
+    using T = typename ST::T;
+    constexpr int kWarps = kAuxBlock / 32;
+    __shared__ double s_sum[kWarps][6];
+    __shared__ unsigned long long s_cnt[kWarps][5];
+    __shared__ unsigned long long s_ext[kWarps][3];
+    __shared__ unsigned int s_hist[ELBM_HIST_BINS + 2];
+
+    for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kAuxBlock) s_hist[b] = 0u;
+    __syncthreads();
+
+    double sum[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long cnt[5] = {0, 0, 0, 0, 0};
+    unsigned long long dmax = 0ULL, amin = ~0ULL, amax = 0ULL;
+
+    for (int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; n < g.N;
+         n += (int64_t)gridDim.x * kAuxBlock) {
+        int x, y, z;
+        node_coords(n, g, x, y, z);
+        T f[Q], xd[Q];
+        pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
+        // FP64 copy of the streamed populations (before f is relaxed).
+        double f64[Q];
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f64[i] = double(f[i]);
+            bad |= !(f64[i] > 0.0) || !isfinite(f64[i]);
+        }
+        int br;
+        const double alpha = double(node_collide<D, T, false>(f, xd, p, &br));
+
+        double r = 0.0, j[3] = {0.0, 0.0, 0.0}, H = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            r += f64[i];
+#pragma unroll
+            for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * f64[i];
+        }
+        sum[0] += r;
+        for (int a = 0; a < D; ++a) sum[1 + a] += j[a];
+        if (bad) {
+            cnt[3] += 1;
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) H += f64[i] * (log(f64[i] / weight(D, i)) - 1.0);
+            // Eq. deltaH3 in FP64 with this node's alpha:
+            // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>, using <f,x> = 0.
+            double un[3] = {0.0, 0.0, 0.0}, feq[Q];
+            for (int a = 0; a < D; ++a) un[a] = j[a] / r;
+            equilibrium64(r, un, feq);
+            const double ab = alpha * p.beta;
+            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const double xi = (feq[i] - f64[i]) / f64[i];
+                s1 += f64[i] * g_entropy(ab * xi);
+                s2 += f64[i] * xi * log1p(xi);
+                s3 += f64[i] * xi * xi;
+            }
+            const double dH = s1 - ab * s2;
+            sum[4] += H;
+            dmax = max(dmax, ordered_bits(dH));
+            if (dH > 1e-6 * s3 && s3 > 0.0) cnt[4] += 1;
+        }
+        sum[5] += alpha;
+        cnt[br == kBranchCutoff ? 0 : (br == kBranchSolved ? 1 : 2)] += 1;
+        const unsigned long long ao = ordered_bits(alpha);
+        amin = min(amin, ao);
+        amax = max(amax, ao);
+        int bin;
+        if (!(alpha >= 1.9)) bin = 0;
+        else if (alpha >= 2.1) bin = ELBM_HIST_BINS + 1;
+        else bin = 1 + min(ELBM_HIST_BINS - 1, int((alpha - 1.9) * (ELBM_HIST_BINS / 0.2)));
+        atomicAdd(&s_hist[bin], 1u);
+    }
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sum[k] = warp_sum(sum[k]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) cnt[k] = warp_sum(cnt[k]);
+    dmax = warp_max(dmax);
+    amin = warp_min(amin);
+    amax = warp_max(amax);
+    if (lane == 0) {
+        for (int k = 0; k < 6; ++k) s_sum[warp][k] = sum[k];
+        for (int k = 0; k < 5; ++k) s_cnt[warp][k] = cnt[k];
+        s_ext[warp][0] = dmax;
+        s_ext[warp][1] = amin;
+        s_ext[warp][2] = amax;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += s_sum[w][threadIdx.x];
+        atomicAdd(&acc->sum[threadIdx.x], v);
+    } else if (threadIdx.x >= 32 && threadIdx.x < 37) {
+        const int k = threadIdx.x - 32;
+        unsigned long long v = 0;
+        for (int w = 0; w < kWarps; ++w) v += s_cnt[w][k];
+        atomicAdd(&acc->cnt[k], v);
+    } else if (threadIdx.x == 64) {
+        unsigned long long a = 0, b = ~0ULL, c = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            a = max(a, s_ext[w][0]);
+            b = min(b, s_ext[w][1]);
+            c = max(c, s_ext[w][2]);
+        }
+        atomicMax(&acc->dH_max_ord, a);
+        atomicMin(&acc->amin_ord, b);
+        atomicMax(&acc->amax_ord, c);
+    }
+    for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kAuxBlock)
+        if (s_hist[b]) atomicAdd(&acc->hist[b], (unsigned long long)s_hist[b]);
+}
+
+// --------------------------------------------------------------------------
+// Launchers (storage dispatch).
+// --------------------------------------------------------------------------
+#define ELBM_STORAGE_SWITCH(storage, CALL)                                                     \
+    switch (storage) {                                                                         \
+    case ELBM_STORE_F64: { using ST = StoreF64; CALL; break; }                                 \
+    case ELBM_STORE_F32: { using ST = StoreF32; CALL; break; }                                 \
+    case ELBM_STORE_F16DEV: { using ST = StoreF16Dev; CALL; break; }                           \
+    case ELBM_STORE_BF16DEV: { using ST = StoreBF16Dev; CALL; break; }                         \
+    default: return cudaErrorInvalidValue;                                                     \
+    }
+
+static inline unsigned blocks_for(int64_t N, int block) { return unsigned((N + block - 1) / block); }
+
+} // namespace ELBM_SUFFIX
+
+#define ELBM_CAT2(a, b) a##_##b
+#define ELBM_CAT(a, b) ELBM_CAT2(a, b)
+
+cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, void *fout,
+                                               const Geometry &g, const CollideParams &p,
+                                               cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    ELBM_STORAGE_SWITCH(storage,
+                        (k_step<ST><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
+                            static_cast<const typename ST::S *>(fin), static_cast<typename ST::S *>(fout),
+                            g, p)));
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_init, ELBM_SUFFIX)(int storage, const double *rho, const double *u,
+                                               void *f, const Geometry &g, double rho_uniform,
+                                               double rho0, cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    ELBM_STORAGE_SWITCH(storage, (k_init<ST><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
+                                     rho, u, static_cast<typename ST::S *>(f), g, rho_uniform, rho0)));
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_moments, ELBM_SUFFIX)(int storage, const void *f, const Geometry &g,
+                                                  double rho0, double *rho_out, double *u_out,
+                                                  cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    ELBM_STORAGE_SWITCH(storage, (k_moments<ST><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
+                                     static_cast<const typename ST::S *>(f), g, rho0, rho_out, u_out)));
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_alpha, ELBM_SUFFIX)(int storage, const void *f, const Geometry &g,
+                                                const CollideParams &p, double *alpha_out,
+                                                uint8_t *flags, cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    ELBM_STORAGE_SWITCH(storage, (k_alpha<ST><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
+                                     static_cast<const typename ST::S *>(f), g, p, alpha_out, flags)));
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_diag, ELBM_SUFFIX)(int storage, const void *f, const Geometry &g,
+                                               const CollideParams &p, DiagAcc *acc, int num_sms,
+                                               cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    unsigned blocks = blocks_for(g.N, kAuxBlock);
+    const unsigned cap = unsigned(num_sms > 0 ? num_sms : 1) * 8u;
+    if (blocks > cap) blocks = cap;
+    ELBM_STORAGE_SWITCH(storage, (k_diag<ST><<<blocks, kAuxBlock, 0, s>>>(
+                                     static_cast<const typename ST::S *>(f), g, p, acc)));
+    return cudaGetLastError();
+}
+
+} // namespace eelbm

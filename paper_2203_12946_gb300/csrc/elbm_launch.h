@@ -1,0 +1,60 @@
+// elbm_launch.h -- internal (C++) interface between the C-ABI layer and the
+// per-lattice kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "elbm.h"
+
+namespace eelbm {
+
+struct Geometry;
+struct CollideParams;
+
+// Device-side accumulator of the diagnostics reduction (library scratch).
+struct DiagAcc {
+    double sum[6];                 // mass, momentum x/y/z, H, sum of alpha
+    unsigned long long cnt[5];     // cutoff, solved, clamped, nonpositive, dH-positive
+    unsigned long long dH_max_ord; // order-preserving encodings of doubles
+    unsigned long long amin_ord;
+    unsigned long long amax_ord;
+    unsigned long long hist[ELBM_HIST_BINS + 2];
+};
+
+// Order-preserving map double -> uint64 (unsigned comparison == double
+// comparison for non-NaN values) and its inverse.
+__host__ __device__ inline unsigned long long ordered_bits(double d)
+{
+    unsigned long long b;
+    memcpy(&b, &d, sizeof b);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+__host__ __device__ inline double from_ordered_bits(unsigned long long o)
+{
+    unsigned long long b = (o >> 63) ? (o & 0x7FFFFFFFFFFFFFFFULL) : ~o;
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+#define ELBM_DECLARE_LAUNCHERS(SUFFIX)                                                               \
+    cudaError_t launch_step_##SUFFIX(int storage, const void *fin, void *fout, const Geometry &g,   \
+                                     const CollideParams &p, cudaStream_t s);                        \
+    cudaError_t launch_init_##SUFFIX(int storage, const double *rho, const double *u, void *f,      \
+                                     const Geometry &g, double rho_uniform, double rho0,             \
+                                     cudaStream_t s);                                                \
+    cudaError_t launch_moments_##SUFFIX(int storage, const void *f, const Geometry &g, double rho0, \
+                                        double *rho_out, double *u_out, cudaStream_t s);            \
+    cudaError_t launch_alpha_##SUFFIX(int storage, const void *f, const Geometry &g,                \
+                                      const CollideParams &p, double *alpha_out, uint8_t *flags,    \
+                                      cudaStream_t s);                                               \
+    cudaError_t launch_diag_##SUFFIX(int storage, const void *f, const Geometry &g,                 \
+                                     const CollideParams &p, DiagAcc *acc, int num_sms,             \
+                                     cudaStream_t s);
+
+ELBM_DECLARE_LAUNCHERS(d2q9)
+ELBM_DECLARE_LAUNCHERS(d3q27)
+
+} // namespace eelbm

@@ -1,0 +1,404 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Both sides receive the same seeded inputs from ``paper_2203_12946_gb300.inputs``;
+the oracle builds its own populations, and where the GPU starts from populations
+they are the oracle's (or the oracle's rounded to the GPU's storage type), never
+the reverse.  Tolerances:
+
+* FP64 path: 1e-12 relative per population (the rounding-order difference of two
+  IEEE double evaluations of the same formulas is ~1e-15 per step);
+* FP32 path: x = f^eq/f - 1 carries ~3e-7 absolute error from the FP32
+  equilibrium, so f* = f (1 + alpha beta x) moves by <= 2 * 3e-7 relative per step;
+  we allow 2e-6 per step on f and 1e-5 relative on u (the stated FP32 target);
+* branch decisions (cutoff, clamp) are integers decided by floating point: each
+  side decides in its own precision, so a node may take the other branch only
+  when its |x|max lies within the decision precision of the 1e-3 threshold
+  (1e-12 for FP64, 1e-6 for FP32); such nodes are excluded from the value check
+  of that step and counted.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2203_12946_gb300 import elbm as E
+from paper_2203_12946_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LAT = {2: E.ELBM_D2Q9, 3: E.ELBM_D3Q27}
+MODES = {"higher": (E.ELBM_ALPHA_HIGHER, O.MODE_HIGHER), "lower": (E.ELBM_ALPHA_LOWER, O.MODE_LOWER),
+         "lbgk": (E.ELBM_ALPHA_LBGK, O.MODE_LBGK)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    E.load()
+
+
+def noisy_state(D, dims, eps, seed=3, u0=0.05, kind="tgv"):
+    """Oracle-made populations: equilibrium of a Taylor-Green field times 1 + eps U(-1,1)."""
+    X, Y, Z = inputs.grid(dims)
+    L = dims[0]
+    if D == 2:
+        rho, u = inputs.taylor_green_2d(X, Y, L, u0=u0)
+    else:
+        rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=u0)
+    f = O.init_equilibrium(D, rho, u)
+    return f * inputs.population_noise(3 ** D, X.size, eps, seed=seed)
+
+
+def gpu_run(D, dims, beta, f0, nsteps, storage="f64", **kw):
+    with E.Simulation(LAT[D], dims, beta, storage=storage, **kw) as sim:
+        sim.set_populations(f0)
+        sim.step(nsteps)
+        f = sim.get_populations().astype(np.float64)
+    return f
+
+
+def xabsmax_of(D, f):
+    """|x|max per node of a pre-collision field (oracle)."""
+    out = np.empty(f.shape[1])
+    for n in range(f.shape[1]):
+        r, u = O.moments(D, f[:, n])
+        out[n] = O.alpha(f[:, n], O.equilibrium(D, r, u), 0.5).xabsmax
+    return out
+
+
+def check_branches(D, f_pre, br_gpu, br_ora, band):
+    """Nodes whose branch differs must sit within `band` of the cutoff; returns the mask of
+    agreeing nodes."""
+    diff = np.nonzero(br_gpu != br_ora)[0]
+    if diff.size:
+        xm = xabsmax_of(D, f_pre[:, diff])
+        assert np.all(np.abs(xm - O.CUTOFF) <= band), (diff[:10], xm[:10])
+    agree = np.ones(br_gpu.size, dtype=bool)
+    agree[diff] = False
+    return agree
+
+
+# ---------------------------------------------------------------------------
+# FP64: one step and several steps, every mode, both b readings, ragged sizes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,dims", [(2, (300, 37, 1)), (3, (37, 19, 11))])
+@pytest.mark.parametrize("mode", ["higher", "lower", "lbgk"])
+@pytest.mark.parametrize("cutoff", [True, False])
+def test_fp64_single_step_every_node(D, dims, mode, cutoff):
+    beta = 0.995
+    f0 = noisy_state(D, dims, 4e-3)
+    gm, om = MODES[mode]
+    f_gpu = gpu_run(D, dims, beta, f0, 1, "f64", alpha_mode=gm, cutoff=cutoff)
+    f_ora, a_ora, br_ora, _ = O.step(D, dims, f0, beta, cutoff=cutoff, mode=om, want_alpha=True)
+    # branch decisions through the alpha field of the same pre-collision state
+    with E.Simulation(LAT[D], dims, beta, storage="f64", alpha_mode=gm, cutoff=cutoff) as sim:
+        sim.set_populations(f0)
+        a_gpu, fl = sim.alpha_field()
+        a_gpu, fl = a_gpu.cpu().numpy(), fl.cpu().numpy()
+    agree = check_branches(D, O.stream(D, dims, f0), fl, br_ora, 1e-12)
+    assert np.max(np.abs(a_gpu[agree] - a_ora[agree])) < 1e-12
+    rel = np.abs(f_gpu - f_ora) / np.abs(f_ora)
+    assert np.max(rel[:, agree]) < 1e-12
+    if mode != "lbgk" and not cutoff:
+        assert np.all(fl != E.ELBM_BRANCH_CUTOFF)  # every node on the closed form
+    if mode == "lbgk":
+        assert np.all(fl == E.ELBM_BRANCH_CUTOFF) and np.all(a_gpu == 2.0)
+
+
+@pytest.mark.parametrize("b_variant", [E.ELBM_B_DERIVED, E.ELBM_B_PRINTED])
+def test_fp64_b_variants(b_variant):
+    D, dims, beta = 3, (21, 17, 9), 0.9
+    f0 = noisy_state(D, dims, 2e-2, seed=5)
+    f_gpu = gpu_run(D, dims, beta, f0, 2, "f64", cutoff=False, b_variant=b_variant)
+    f_ora, *_ = O.step(D, dims, f0, beta, cutoff=False, b_variant=b_variant, nsteps=2)
+    assert np.max(np.abs(f_gpu - f_ora) / f_ora) < 1e-12
+
+
+@pytest.mark.parametrize("D,dims,nsteps", [(2, (96, 53, 1), 25), (3, (23, 18, 13), 8)])
+def test_fp64_multistep(D, dims, nsteps):
+    beta = 0.999
+    f0 = noisy_state(D, dims, 1e-2, seed=9)
+    f_gpu = gpu_run(D, dims, beta, f0, nsteps, "f64", cutoff=False)
+    f_ora, *_ = O.step(D, dims, f0, beta, cutoff=False, nsteps=nsteps)
+    assert np.max(np.abs(f_gpu - f_ora) / f_ora) < 1e-12
+
+
+def test_config1_taylor_green_64_fp64_1000_steps():
+    """D2Q9 64^2 Taylor-Green, u0 = 0.01, beta = 0.9, 1000 steps, FP64: u within 1e-12
+    relative of the oracle with every node on the closed-form path (cutoff off), and with
+    the paper's cutoff on (both sides decide in FP64)."""
+    L, beta = 64, 0.9
+    dims = (L, L, 1)
+    X, Y, _ = inputs.grid(dims)
+    rho, u = inputs.taylor_green_2d(X, Y, L, u0=0.01)
+    for cutoff in (False, True):
+        with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64", cutoff=cutoff) as sim:
+            sim.init_equilibrium(rho, u)
+            f_init = sim.get_populations()
+            sim.step(1000)
+            r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
+        f_o0 = O.init_equilibrium(2, rho, u)
+        assert np.max(np.abs(f_init - f_o0) / f_o0) < 1e-15
+        f_o, *_ = O.step(2, dims, f_o0, beta, cutoff=cutoff, nsteps=1000)
+        r_o, u_o = O.moments_field(2, f_o)
+        assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) < 1e-12
+        assert np.max(np.abs(r_g - r_o)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# FP32
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,dims", [(2, (300, 37, 1)), (3, (37, 19, 11))])
+@pytest.mark.parametrize("cutoff", [True, False])
+def test_fp32_single_step(D, dims, cutoff):
+    beta = 0.999
+    f0 = noisy_state(D, dims, 4e-3).astype(np.float32)
+    f_gpu = gpu_run(D, dims, beta, f0, 1, "f32", cutoff=cutoff)
+    f_in = f0.astype(np.float64)
+    f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=cutoff, want_alpha=True)
+    with E.Simulation(LAT[D], dims, beta, storage="f32", cutoff=cutoff) as sim:
+        sim.set_populations(f0)
+        a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]
+    agree = check_branches(D, O.stream(D, dims, f_in), fl, br_ora, 1e-6)
+    assert np.max(np.abs(a_gpu[agree] - a_ora[agree])) < 2e-5
+    rel = np.abs(f_gpu - f_ora) / f_ora
+    assert np.max(rel[:, agree]) < 2e-6
+
+
+@pytest.mark.parametrize("D,dims,nsteps", [(2, (128, 77, 1), 20), (3, (29, 23, 17), 10)])
+def test_fp32_multistep_velocity(D, dims, nsteps):
+    beta = 0.999
+    f0 = noisy_state(D, dims, 3e-3, seed=13).astype(np.float32)
+    for cutoff in (False, True):
+        with E.Simulation(LAT[D], dims, beta, storage="f32", cutoff=cutoff) as sim:
+            sim.set_populations(f0)
+            sim.step(nsteps)
+            r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
+            f_g = sim.get_populations().astype(np.float64)
+        f_o, *_ = O.step(D, dims, f0.astype(np.float64), beta, cutoff=cutoff, nsteps=nsteps)
+        r_o, u_o = O.moments_field(D, f_o)
+        assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) < 1e-5
+        assert np.max(np.abs(r_g - r_o)) < 1e-5
+        assert np.max(np.abs(f_g - f_o) / f_o) < nsteps * 2e-6
+
+
+def test_fp32_full_size_sampled_nodes():
+    """D3Q27 256^3 Taylor-Green (u0 = 0.05, beta = 0.999) in the benchmark's launch
+    configuration, 3 steps: sampled nodes against the oracle, which recomputes each from a
+    9^3 box of its own initial state (a node after k steps depends only on its (2k+1)^3
+    neighbourhood, so the box's wrap-around never reaches it)."""
+    L, beta, k = 256, 0.999, 3
+    dims = (L, L, L)
+    X, Y, Z = inputs.grid(dims)
+    rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=0.05)
+    with E.Simulation(E.ELBM_D3Q27, dims, beta, storage="f32") as sim:
+        sim.init_equilibrium(rho, u)
+        d0 = sim.diagnostics()
+        sim.step(k)
+        f_gpu = sim.get_populations()
+        d1 = sim.diagnostics(with_hist=True)
+    del X, Y, Z, rho, u
+    rng = np.random.default_rng(17)
+    samples = rng.integers(0, L, size=(120, 3))
+    samples[:8] = [[0, 0, 0], [L - 1, L - 1, L - 1], [0, L - 1, 5], [L - 1, 0, 200],
+                   [128, 0, L - 1], [1, 2, 3], [255, 128, 0], [64, 64, 64]]
+    B = 2 * k + 3
+    off = np.arange(B) - B // 2
+    bz, by, bx = np.meshgrid(off, off, off, indexing="ij")
+    worst = 0.0
+    for (sx, sy, sz) in samples:
+        gx, gy, gz = (sx + bx.ravel()) % L, (sy + by.ravel()) % L, (sz + bz.ravel()) % L
+        r, uu = inputs.taylor_green_3d(gx, gy, gz, L, u0=0.05)
+        fb = O.init_equilibrium(3, r, uu).astype(np.float32).astype(np.float64)
+        fb, *_ = O.step(3, (B, B, B), fb, beta, nsteps=k)
+        centre = (B // 2 * B + B // 2) * B + B // 2
+        n = (sz * L + sy) * L + sx
+        got = f_gpu[:, n].astype(np.float64)
+        want = fb[:, centre]
+        worst = max(worst, np.max(np.abs(got - want) / want))
+    assert worst < k * 2e-6
+    # properties over the whole field
+    assert abs(d1["mass"] - d0["mass"]) < 1e-6 * d0["mass"]
+    assert np.max(np.abs(np.array(d1["momentum"]) - np.array(d0["momentum"]))) < 1e-6 * d0["mass"]
+    assert d1["H"] <= d0["H"] + 1e-7 * abs(d0["H"])
+    # with the paper's cutoff, alpha = 2 need not satisfy the H theorem on near-equilibrium
+    # nodes (the guarantee is for alpha_H), so violations may occur only there
+    assert d1["n_nonpositive"] == 0 and d1["n_dH_positive"] <= d1["n_cutoff"]
+    assert d1["alpha_hist"].sum() == L ** 3
+    assert d1["n_solved"] > 0 and 1.9 < d1["alpha_min"] <= d1["alpha_max"] < 2.1
+
+
+# ---------------------------------------------------------------------------
+# deviation storage (FP16 / BF16 of f - w rho0, FP32 arithmetic)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("storage,mant_bits", [("f16dev", 10), ("bf16dev", 7)])
+def test_deviation_storage_single_step(storage, mant_bits):
+    D, dims, beta = 3, (31, 17, 9), 0.999
+    c, w = O.lattice(D)
+    f0 = noisy_state(D, dims, 3e-3, seed=21)
+    dev = f0 - w[:, None]
+    with E.Simulation(LAT[D], dims, beta, storage=storage) as sim:
+        # the stored deviation, rounded to nearest by numpy
+        if storage == "f16dev":
+            q = dev.astype(np.float16)
+            deq = q.astype(np.float64) + w[:, None]
+            sim.set_populations(q)
+        else:
+            b = dev.astype(np.float32).view(np.uint32)
+            b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)  # RNE to bf16
+            deq = (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64) + w[:, None]
+            sim.set_populations(b)
+        sim.step(1)
+        raw = sim.get_populations()
+    if storage == "f16dev":
+        got = raw.astype(np.float64) + w[:, None]
+    else:
+        got = (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64) + w[:, None]
+    want, *_ = O.step(D, dims, deq, beta, nsteps=1)
+    err = np.abs(got - want)
+    bound = 2.0 ** -(mant_bits + 1) * np.abs(want - w[:, None]) * 1.01 + 4e-6 * want + 1e-7
+    assert np.all(err <= bound)
+
+
+# ---------------------------------------------------------------------------
+# companions: init, moments, alpha field, diagnostics, edge cases
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_init_and_moments(storage):
+    D, dims = 3, (19, 13, 7)
+    rng = np.random.default_rng(23)
+    N = int(np.prod(dims))
+    rho = 1 + 0.05 * (2 * rng.random(N) - 1)
+    u = 0.1 * rng.standard_normal((3, N))
+    with E.Simulation(E.ELBM_D3Q27, dims, 0.9, storage=storage) as sim:
+        sim.init_equilibrium(rho, u)
+        f = sim.get_populations().astype(np.float64)
+        r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
+    f_o = O.init_equilibrium(3, rho, u)
+    tol = 1e-15 if storage == "f64" else 6e-8
+    assert np.max(np.abs(f - f_o) / f_o) < tol
+    r_o, u_o = O.moments_field(3, f)
+    assert np.max(np.abs(r_g - r_o)) < 1e-14 and np.max(np.abs(u_g - u_o)) < 1e-14
+
+
+def test_diagnostics_against_oracle():
+    D, dims, beta = 2, (160, 90, 1), 0.995
+    f0 = noisy_state(D, dims, 5e-3, seed=29)
+    with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64", cutoff=False) as sim:
+        sim.set_populations(f0)
+        d = sim.diagnostics(with_hist=True)
+    c, w = O.lattice(D)
+    fs = O.stream(D, dims, f0)
+    _, a, br, _ = O.collide(D, fs, beta, cutoff=False, want_alpha=True)
+    _, _, _, dH = O.collide(D, fs, beta, cutoff=False, want_dH=True)
+    assert abs(d["mass"] - f0.sum()) < 1e-12 * f0.sum()
+    assert np.allclose(d["momentum"][:2], (c.T @ f0).sum(axis=1), rtol=0, atol=1e-11)
+    assert abs(d["H"] - O.H_total(D, f0)) < 1e-12 * abs(d["H"])
+    assert d["n_solved"] == np.sum(br == O.BRANCH_SOLVED)
+    assert d["n_clamped"] == np.sum(br == O.BRANCH_CLAMPED)
+    assert abs(d["alpha_min"] - a.min()) < 1e-12 and abs(d["alpha_max"] - a.max()) < 1e-12
+    assert abs(d["alpha_mean"] - a.mean()) < 1e-12
+    assert abs(d["dH_max"] - dH.max()) < 1e-14 and d["dH_max"] <= 0
+    assert d["n_dH_positive"] == 0 and d["n_nonpositive"] == 0
+    hist = d["alpha_hist"]
+    assert hist.sum() == a.size
+    edges = np.linspace(1.9, 2.1, E.ELBM_HIST_BINS + 1)
+    inner = np.histogram(a[(a >= 1.9) & (a < 2.1)], bins=edges)[0]
+    # bin edges are decided in two different floating-point formulas: allow a few moves
+    assert np.sum(np.abs(hist[1:-1] - inner)) <= 4
+
+
+def test_nonphysical_state_is_reported():
+    D, dims = 2, (16, 8, 1)
+    f0 = noisy_state(D, dims, 1e-3)
+    f0[4, 37] = -1e-3
+    with E.Simulation(E.ELBM_D2Q9, dims, 0.9, storage="f64") as sim:
+        sim.set_populations(f0)
+        with pytest.raises(E.ElbmError) as ei:
+            sim.diagnostics()
+        assert ei.value.code == E.ELBM_ERR_NONPHYSICAL
+        d = sim.diagnostics(allow_nonphysical=True)
+        assert d["n_nonpositive"] >= 1
+
+
+def test_clamp_branch_matches_oracle():
+    """Far from equilibrium (noise 0.9 on every population) the positivity clamp acts on
+    many nodes; GPU and oracle agree on which and on the clamped alpha (FP64)."""
+    D, dims, beta = 2, (64, 48, 1), 0.99
+    f0 = noisy_state(D, dims, 0.9, seed=31)
+    f_gpu = gpu_run(D, dims, beta, f0, 1, "f64")
+    f_ora, a_ora, br_ora, _ = O.step(D, dims, f0, beta, want_alpha=True)
+    with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64") as sim:
+        sim.set_populations(f0)
+        a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]
+    assert np.sum(br_ora == O.BRANCH_CLAMPED) > 20
+    assert np.array_equal(fl, br_ora)
+    assert np.max(np.abs(a_gpu - a_ora)) < 1e-12
+    assert np.max(np.abs(f_gpu - f_ora) / f_ora) < 1e-11
+    assert np.all(f_gpu > 0)
+
+
+@pytest.mark.parametrize("D,dims", [(2, (1, 1, 1)), (2, (1, 7, 1)), (2, (5, 1, 1)),
+                                    (3, (1, 1, 1)), (3, (1, 4, 3)), (3, (2, 2, 2))])
+def test_degenerate_domains(D, dims):
+    """Periodic wrap onto itself (a side of 1 or 2 nodes)."""
+    f0 = noisy_state(D, dims, 1e-2, seed=37)
+    f_gpu = gpu_run(D, dims, 0.97, f0, 3, "f64", cutoff=False)
+    f_ora, *_ = O.step(D, dims, f0, 0.97, cutoff=False, nsteps=3)
+    assert np.max(np.abs(f_gpu - f_ora) / f_ora) < 1e-12
+
+
+def test_zero_steps_and_uniform_fixed_point():
+    D, dims = 3, (9, 8, 7)
+    N = int(np.prod(dims))
+    u = np.repeat(np.array([[0.03], [-0.02], [0.01]]), N, axis=1)
+    with E.Simulation(E.ELBM_D3Q27, dims, 0.95, storage="f64") as sim:
+        sim.init_equilibrium(np.full(N, 1.2), u)
+        f0 = sim.get_populations()
+        sim.step(0)
+        assert sim.steps == 0 and np.array_equal(sim.get_populations(), f0)
+        sim.step(5)
+        f5 = sim.get_populations()
+        a, fl = [t.cpu().numpy() for t in sim.alpha_field()]
+    assert np.max(np.abs(f5 - f0)) < 1e-16
+    assert np.all(a == 2.0) and np.all(fl == E.ELBM_BRANCH_CUTOFF)
+
+
+@pytest.mark.parametrize("beta", [0.02, 0.5, 0.99999])
+def test_beta_extremes(beta):
+    D, dims = 2, (40, 30, 1)
+    f0 = noisy_state(D, dims, 1e-2, seed=41)
+    f_gpu = gpu_run(D, dims, beta, f0, 2, "f64", cutoff=False)
+    f_ora, *_ = O.step(D, dims, f0, beta, cutoff=False, nsteps=2)
+    assert np.max(np.abs(f_gpu - f_ora) / f_ora) < 1e-12
+
+
+def test_host_buffers_end_to_end():
+    """The C-ABI host-memory forms (init from host arrays, moments into host arrays)."""
+    D, dims, beta = 2, (48, 40, 1), 0.99
+    X, Y, _ = inputs.grid(dims)
+    rho, u = inputs.shear_layer_2d(X, Y, 48)
+    h = E.elbm_create(E.ELBM_D2Q9, dims, beta, opts=_opts(E.ELBM_STORE_F64))
+    try:
+        E.elbm_init_equilibrium(h, np.ascontiguousarray(rho), np.ascontiguousarray(u), E.ELBM_MEM_HOST)
+        E.elbm_step(h, 4)
+        r = np.empty(X.size)
+        uu = np.empty((2, X.size))
+        E.elbm_moments(h, r, uu, E.ELBM_MEM_HOST)
+        assert E.elbm_step_count(h) == 4
+    finally:
+        E.elbm_destroy(h)
+    f_o, *_ = O.step(2, dims, O.init_equilibrium(2, rho, u), beta, nsteps=4)
+    r_o, u_o = O.moments_field(2, f_o)
+    assert np.max(np.abs(uu - u_o)) < 1e-12 and np.max(np.abs(r - r_o)) < 1e-12
+
+
+def _opts(storage):
+    o = E.elbm_default_opts()
+    o.storage = storage
+    return o
