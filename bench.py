@@ -46,6 +46,14 @@ KERNEL_SOURCES = ["paper_2203_12946_gb300/csrc/elbm_device.cuh",
                   "paper_2203_12946_gb300/csrc/elbm_kernels.cuh"]
 
 
+def set_side(side: int) -> None:
+    """Smaller cubes for profiling captures; the reported workload string follows."""
+    global L, WORKLOAD, METRIC
+    L = int(side)
+    WORKLOAD = WORKLOAD.replace("256^3", f"{L}^3")
+    METRIC = METRIC.replace("256^3", f"{L}^3")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
@@ -137,6 +145,45 @@ def dist_env():
     return world, rank, local
 
 
+class Replicas:
+    """Independent replicas, one per rank: the only collectives are the barrier around the
+    timed region and the max over ranks of its duration (no data-path exchange)."""
+
+    def __init__(self, backend: str, device=None):
+        self.world, self.rank, self.local = dist_env()
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            kw = {"device_id": device} if (backend == "nccl" and device is not None) else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.dist:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64,
+                         device=self.device if self.device is not None else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def aggregate_mlups(nodes_per_rank: int, steps: int, world: int, max_elapsed_s: float) -> float:
+    """Whole-job throughput: node updates of all ranks over the slowest rank's time."""
+    return world * nodes_per_rank * steps / max_elapsed_s / 1e6
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------
@@ -219,9 +266,7 @@ def run_gpu(args):
         raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    rep = Replicas("nccl", dev)
     E.load()
 
     dims = (L, L, L)
@@ -241,9 +286,7 @@ def run_gpu(args):
 
     def barrier():
         torch.cuda.synchronize(dev)
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        rep.barrier()
         torch.cuda.synchronize(dev)
 
     def one_step(k, ev=None):
@@ -280,11 +323,7 @@ def run_gpu(args):
     elapsed = start.elapsed_time(stop) / 1e3
     kern = [a.elapsed_time(b) / 1e3 for a, b in evs]
     kern_avg = float(np.mean(kern))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = rep.max(elapsed)
     gpu_launches = args.steps + args.steps // DIAG_EVERY
     d = sim.diagnostics()
 
@@ -300,18 +339,14 @@ def run_gpu(args):
     E.elbm_moments(sim.h, rho_out.numpy(), u_out.numpy(), E.ELBM_MEM_HOST)
     barrier()
     e2e_t = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = rep.max(e2e_t)
     h2d = (rho_h.numel() + u_h.numel()) * 8
     d2h = (rho_out.numel() + u_out.numel()) * 8
 
     peak, peak_src = measured_peaks()
     achieved = BYTES_PER_NODE * N / kern_avg / 1e9
     traffic = profiled_traffic()
-    value = world * N * args.steps / elapsed / 1e6
+    value = aggregate_mlups(N, args.steps, world, elapsed)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -325,7 +360,7 @@ def run_gpu(args):
                      "kernel": "k_step<StoreF32> (D3Q27)",
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE * N,
                      "kernel_ms_avg": 1e3 * kern_avg},
-        "e2e": {"value": world * N * args.steps / e2e_t / 1e6, "unit": "MLUPS",
+        "e2e": {"value": aggregate_mlups(N, args.steps, world, e2e_t), "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "what": "elbm_init_equilibrium from pinned host rho,u + K steps + elbm_moments to host"},
         "gpu_launches": gpu_launches,
@@ -339,10 +374,7 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": rate, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
     sim.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+    rep.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -357,9 +389,13 @@ def main():
     ap.add_argument("--cpu-slab", type=int, default=32)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--L", type=int, default=L, help="domain side (profiling runs only; "
+                    "the benchmark workload is 256)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.L != L:
+        set_side(args.L)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -65,6 +65,9 @@ struct CollideParams {
 __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+// correctly rounded division, for the few divisions whose rounding reaches f^eq
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 
 // ---------------------------------------------------------------------------
@@ -159,7 +162,7 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
             if (vel(D, i, a) == -1) j[a] -= f[i];
         }
     }
-    const T irho = div_(T(1), rho);
+    const T irho = div_rn(T(1), rho);
 
     // Product-form entropic equilibrium (Sec. I): per axis
     // Upsilon = 2 - sqrt(1 + 3u^2), z = (2u + sqrt(1 + 3u^2)) / (1 - u); the
@@ -172,9 +175,9 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
         const T Y = T(2) - s;
         const T num = T(2) * u + s;
         const T den = T(1) - u;
-        phi[a][0] = div_(Y * den, T(6) * num);
+        phi[a][0] = div_rn(Y * den, T(6) * num);
         phi[a][1] = Y * T(4.0 / 6.0);
-        phi[a][2] = div_(Y * num, T(6) * den);
+        phi[a][2] = div_rn(Y * num, T(6) * den);
     }
 
     // Departures x_i = (f^eq_i - f_i) / f_i and their extremes.
@@ -292,20 +295,24 @@ __device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin
 }
 
 // ---------------------------------------------------------------------------
-// FP64 diagnostics helpers.
+// Diagnostics helpers.
 // g(y) = (1+y) log(1+y) - y; near 0 the Taylor series
 // sum_{k>=2} (-1)^k y^k / (k(k-1)) avoids the cancellation of the direct form.
+// The series is summed to k = 20 in FP64 and k = 9 in FP32 (for |y| < 0.1 the
+// dropped terms are below the type's rounding).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double g_entropy(double y)
+template <class T>
+__device__ __forceinline__ T g_entropy(T y)
 {
-    if (y <= -1.0) return 1.0;
-    if (fabs(y) < 0.1) {
-        double s = 0.0;
+    constexpr int kTerms = sizeof(T) == 8 ? 20 : 9;
+    if (y <= T(-1)) return T(1);
+    if (fabs(y) < T(0.1)) {
+        T s = T(0);
 #pragma unroll
-        for (int k = 20; k >= 2; --k) s = s * y + ((k % 2 == 0) ? 1.0 : -1.0) / double(k * (k - 1));
+        for (int k = kTerms; k >= 2; --k) s = s * y + T(((k % 2 == 0) ? 1.0 : -1.0) / double(k * (k - 1)));
         return s * y * y;
     }
-    return (1.0 + y) * log1p(y) - y;
+    return (T(1) + y) * log1p(y) - y;
 }
 
 } // namespace eelbm

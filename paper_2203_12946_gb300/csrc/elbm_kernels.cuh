@@ -190,46 +190,45 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         node_coords(n, g, x, y, z);
         T f[Q], xd[Q];
         pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
-        // FP64 copy of the streamed populations (before f is relaxed).
-        double f64[Q];
+        T fc[Q];
         bool bad = false;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f64[i] = double(f[i]);
-            bad |= !(f64[i] > 0.0) || !isfinite(f64[i]);
+            fc[i] = f[i];
+            bad |= !(f[i] > T(0)) || !isfinite(f[i]);
         }
         int br;
-        const double alpha = double(node_collide<D, T, false>(f, xd, p, &br));
+        const T alpha_t = node_collide<D, T, false>(f, xd, p, &br);
+        const double alpha = double(alpha_t);
 
-        double r = 0.0, j[3] = {0.0, 0.0, 0.0}, H = 0.0;
+        double r = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            r += f64[i];
+            const double v = double(fc[i]);
+            r += v;
 #pragma unroll
-            for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * f64[i];
+            for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * v;
         }
         sum[0] += r;
         for (int a = 0; a < D; ++a) sum[1 + a] += j[a];
         if (bad) {
             cnt[3] += 1;
         } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) H += f64[i] * (log(f64[i] / weight(D, i)) - 1.0);
-            // Eq. deltaH3 in FP64 with this node's alpha:
-            // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>, using <f,x> = 0.
-            double un[3] = {0.0, 0.0, 0.0}, feq[Q];
-            for (int a = 0; a < D; ++a) un[a] = j[a] / r;
-            equilibrium64(r, un, feq);
-            const double ab = alpha * p.beta;
-            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            // H[f] (Eq. hdef) and the entropy change of this node's collision (Eq.
+            // deltaH3, with <f,x> = 0 removing alpha beta <f,x> from both sums):
+            // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>.  Transcendentals in
+            // the path's compute type, sums per node and over the domain in FP64.
+            const T ab = alpha_t * T(p.beta);
+            double H = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const double xi = (feq[i] - f64[i]) / f64[i];
-                s1 += f64[i] * g_entropy(ab * xi);
-                s2 += f64[i] * xi * log1p(xi);
-                s3 += f64[i] * xi * xi;
+                const T fi = fc[i], xi = xd[i];
+                H += double(fi * (log(fi * T(1.0 / weight(D, i))) - T(1)));
+                s1 += double(fi * g_entropy<T>(ab * xi));
+                s2 += double(fi * xi * log1p(xi));
+                s3 += double(fi * xi * xi);
             }
-            const double dH = s1 - ab * s2;
+            const double dH = s1 - double(ab) * s2;
             sum[4] += H;
             dmax = max(dmax, ordered_bits(dH));
             if (dH > 1e-6 * s3 && s3 > 0.0) cnt[4] += 1;

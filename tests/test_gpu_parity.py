@@ -168,8 +168,36 @@ def test_fp32_single_step(D, dims, cutoff):
     assert np.max(rel[:, agree]) < 2e-6
 
 
+@pytest.mark.parametrize("D,L,nsteps", [(2, 96, 40), (3, 32, 20)])
+def test_fp32_taylor_green_velocity(D, L, nsteps):
+    """Taylor-Green vortex (u0 = 0.05, beta = 0.999) from the equilibrium, FP32 storage and
+    arithmetic: u within 1e-5 relative (L2) of the FP64 oracle started from the same
+    FP32-rounded populations, with the closed-form alpha active on most nodes."""
+    beta = 0.999
+    dims = (L, L, 1) if D == 2 else (L, L, L)
+    X, Y, Z = inputs.grid(dims)
+    rho, u = (inputs.taylor_green_2d(X, Y, L, u0=0.05) if D == 2
+              else inputs.taylor_green_3d(X, Y, Z, L, u0=0.05))
+    with E.Simulation(LAT[D], dims, beta, storage="f32") as sim:
+        sim.init_equilibrium(rho, u)
+        f_init = sim.get_populations().astype(np.float64)
+        sim.step(nsteps)
+        r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
+        d = sim.diagnostics()
+    f_o0 = O.init_equilibrium(D, rho, u).astype(np.float32).astype(np.float64)
+    assert np.array_equal(f_init, f_o0)
+    f_o, *_ = O.step(D, dims, f_o0, beta, nsteps=nsteps)
+    r_o, u_o = O.moments_field(D, f_o)
+    assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) < 1e-5
+    assert np.max(np.abs(r_g - r_o)) < 1e-5
+    assert d["n_solved"] > 0.5 * X.size
+
+
 @pytest.mark.parametrize("D,dims,nsteps", [(2, (128, 77, 1), 20), (3, (29, 23, 17), 10)])
-def test_fp32_multistep_velocity(D, dims, nsteps):
+def test_fp32_noisy_multistep(D, dims, nsteps):
+    """Strongly non-equilibrium start (0.3% noise on every population).  The FP32 rounding of
+    f^eq (a few ulp per population) breaks the collision's momentum balance by at most
+    ~D * 1e-7 rho per node and step, so |u_gpu - u_oracle| <= 2e-7 D nsteps."""
     beta = 0.999
     f0 = noisy_state(D, dims, 3e-3, seed=13).astype(np.float32)
     for cutoff in (False, True):
@@ -180,55 +208,58 @@ def test_fp32_multistep_velocity(D, dims, nsteps):
             f_g = sim.get_populations().astype(np.float64)
         f_o, *_ = O.step(D, dims, f0.astype(np.float64), beta, cutoff=cutoff, nsteps=nsteps)
         r_o, u_o = O.moments_field(D, f_o)
-        assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) < 1e-5
+        assert np.max(np.abs(u_g - u_o)) < 2e-7 * D * nsteps
         assert np.max(np.abs(r_g - r_o)) < 1e-5
         assert np.max(np.abs(f_g - f_o) / f_o) < nsteps * 2e-6
 
 
 def test_fp32_full_size_sampled_nodes():
     """D3Q27 256^3 Taylor-Green (u0 = 0.05, beta = 0.999) in the benchmark's launch
-    configuration, 3 steps: sampled nodes against the oracle, which recomputes each from a
-    9^3 box of its own initial state (a node after k steps depends only on its (2k+1)^3
-    neighbourhood, so the box's wrap-around never reaches it)."""
-    L, beta, k = 256, 0.999, 3
+    configuration.  After k = 8 steps, sampled nodes against the oracle, which recomputes
+    each from a (2k+3)^3 box of its own initial state (a node after k steps depends only on
+    its (2k+1)^3 neighbourhood, so the box's wrap-around never reaches it).  Then 300
+    steps in all: conservation, H non-increasing, positivity and the alpha range over the
+    whole field (the closed-form branch takes over as the non-equilibrium part grows)."""
+    L, beta, k = 256, 0.999, 8
     dims = (L, L, L)
     X, Y, Z = inputs.grid(dims)
     rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=0.05)
     with E.Simulation(E.ELBM_D3Q27, dims, beta, storage="f32") as sim:
         sim.init_equilibrium(rho, u)
+        del X, Y, Z, rho, u
         d0 = sim.diagnostics()
         sim.step(k)
         f_gpu = sim.get_populations()
+        dk = sim.diagnostics()
+        sim.step(300 - k)
         d1 = sim.diagnostics(with_hist=True)
-    del X, Y, Z, rho, u
     rng = np.random.default_rng(17)
-    samples = rng.integers(0, L, size=(120, 3))
+    samples = rng.integers(0, L, size=(60, 3))
     samples[:8] = [[0, 0, 0], [L - 1, L - 1, L - 1], [0, L - 1, 5], [L - 1, 0, 200],
                    [128, 0, L - 1], [1, 2, 3], [255, 128, 0], [64, 64, 64]]
     B = 2 * k + 3
     off = np.arange(B) - B // 2
     bz, by, bx = np.meshgrid(off, off, off, indexing="ij")
+    centre = (B // 2 * B + B // 2) * B + B // 2
     worst = 0.0
     for (sx, sy, sz) in samples:
         gx, gy, gz = (sx + bx.ravel()) % L, (sy + by.ravel()) % L, (sz + bz.ravel()) % L
         r, uu = inputs.taylor_green_3d(gx, gy, gz, L, u0=0.05)
         fb = O.init_equilibrium(3, r, uu).astype(np.float32).astype(np.float64)
         fb, *_ = O.step(3, (B, B, B), fb, beta, nsteps=k)
-        centre = (B // 2 * B + B // 2) * B + B // 2
         n = (sz * L + sy) * L + sx
-        got = f_gpu[:, n].astype(np.float64)
-        want = fb[:, centre]
-        worst = max(worst, np.max(np.abs(got - want) / want))
+        worst = max(worst, np.max(np.abs(f_gpu[:, n].astype(np.float64) - fb[:, centre]) / fb[:, centre]))
     assert worst < k * 2e-6
-    # properties over the whole field
-    assert abs(d1["mass"] - d0["mass"]) < 1e-6 * d0["mass"]
-    assert np.max(np.abs(np.array(d1["momentum"]) - np.array(d0["momentum"]))) < 1e-6 * d0["mass"]
-    assert d1["H"] <= d0["H"] + 1e-7 * abs(d0["H"])
-    # with the paper's cutoff, alpha = 2 need not satisfy the H theorem on near-equilibrium
-    # nodes (the guarantee is for alpha_H), so violations may occur only there
-    assert d1["n_nonpositive"] == 0 and d1["n_dH_positive"] <= d1["n_cutoff"]
+    for d in (dk, d1):
+        assert abs(d["mass"] - d0["mass"]) < 1e-6 * d0["mass"]
+        assert np.max(np.abs(np.array(d["momentum"]) - np.array(d0["momentum"]))) < 1e-6 * d0["mass"]
+        assert d["n_nonpositive"] == 0
+        # with the paper's cutoff, alpha = 2 need not satisfy the H theorem on
+        # near-equilibrium nodes (the guarantee is for alpha_H): violations only there
+        assert d["n_dH_positive"] <= d["n_cutoff"]
+    assert dk["H"] <= d0["H"] and d1["H"] <= dk["H"]
     assert d1["alpha_hist"].sum() == L ** 3
-    assert d1["n_solved"] > 0 and 1.9 < d1["alpha_min"] <= d1["alpha_max"] < 2.1
+    assert d1["n_solved"] > L ** 3 // 2 and 1.9 < d1["alpha_min"] <= d1["alpha_max"] < 2.1
 
 
 # ---------------------------------------------------------------------------
@@ -365,7 +396,8 @@ def test_zero_steps_and_uniform_fixed_point():
         sim.step(5)
         f5 = sim.get_populations()
         a, fl = [t.cpu().numpy() for t in sim.alpha_field()]
-    assert np.max(np.abs(f5 - f0)) < 1e-16
+    # re-deriving f^eq from the moments of f^eq reproduces it to a few ulp per step
+    assert np.max(np.abs(f5 - f0) / f0) < 1e-14
     assert np.all(a == 2.0) and np.all(fl == E.ELBM_BRANCH_CUTOFF)
 
 
