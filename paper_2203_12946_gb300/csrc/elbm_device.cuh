@@ -39,6 +39,15 @@ __host__ __device__ constexpr double weight(int D, int i)
     return w;
 }
 
+// Sum of the weights after rounding to T, minus one (zero in exact arithmetic).
+template <int D, class T>
+__host__ __device__ constexpr double weight_sum_error()
+{
+    double s = 0.0;
+    for (int i = 0; i < (D == 2 ? 9 : 27); ++i) s += double(T(weight(D, i)));
+    return s - 1.0;
+}
+
 struct Geometry {
     int nx, ny, nz;
     int64_t N;
@@ -137,9 +146,25 @@ __device__ __forceinline__ T quad_root(T a, T b, T c)
 // Per-node collision on registers.
 //   in : f[Q]  pre-collision populations
 //   out: f[Q]  post-collision populations f* = f + alpha beta (f^eq - f)
+//              (only when kRelax)
 //        x[Q]  departures x_i = f^eq_i / f_i - 1 (Eq. xdef)
 //        returns alpha; *branch receives kBranch*
-// The relaxation uses f^eq - f = x f, so only f and x stay live.
+//
+// Evaluation order (the arithmetic is the paper's; only the grouping differs):
+//  * f^eq - f is formed in deviation form.  With d_i = f_i - w_i,
+//    rho = 1 + drho, and per axis eps(c) = Upsilon z^c - 1 (c = -1, 0, 1),
+//    f^eq_i - f_i = w_i (drho + rho E_i) - d_i,  E_i = prod_a (1 + eps_a(c_ia)) - 1,
+//    so no rounding happens at the scale of w_i (FP32 keeps ~u times more
+//    digits of f^eq - f than the product form evaluated directly).  The axis
+//    factors use Upsilon - 1 = -3u^2/(1+s), z - 1 = (3u + 3u^2/(1+s))/(1-u) and
+//    1/z - 1 = -(3u + 3u^2/(1+s))/(2u+s), s = sqrt(1 + 3u^2).
+//  * The Gauss-Legendre denominator factors: 60 + 90x + 36x^2 + 3x^3 =
+//    (2 + x)(30 + 30x + 3x^2), so the c1 and c terms share one reciprocal.
+//  * The Omega+ bracket 2/(4+t) + 1/(4+2t) + 2/(4+3t) is the single rational
+//    (80 + 80t + 19t^2) / (64 + 96t + 44t^2 + 6t^3).
+//  * a is assembled from the Omega- power sums S_k = <f, x^k>_- (k = 3..6);
+//    a1 = S3/2 and a2 = beta^2 S3/6.
+//  * The relaxation uses f^eq - f = x f, so only f and x stay live.
 // ---------------------------------------------------------------------------
 template <int D, class T, bool kRelax = true>
 __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q],
@@ -148,48 +173,81 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
     constexpr int Q = Lattice<D>::Q;
     const T beta = T(p.beta);
 
-    // Moments (Sec. I): rho = <f,1>, rho u = <f,c>.
-    T rho = T(0);
-    T j[D];
+    // Deviations from the weights and the moments (Sec. I): rho = <f,1>,
+    // rho u = <f,c> = <d,c> (the weights carry no momentum).  Sums are taken
+    // along the last axis first, then the middle, then the first.
+    T dev[Q];
 #pragma unroll
-    for (int a = 0; a < D; ++a) j[a] = T(0);
+    for (int i = 0; i < Q; ++i) dev[i] = f[i] - T(weight(D, i));
+    constexpr int P = Q / 3; // columns along the last axis
+    T s0[P], s1[P];          // per column: sum over c_last, and (c_last=+1) - (c_last=-1)
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        rho += f[i];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            if (vel(D, i, a) == 1) j[a] += f[i];
-            if (vel(D, i, a) == -1) j[a] -= f[i];
-        }
+    for (int k = 0; k < P; ++k) {
+        s0[k] = dev[3 * k] + dev[3 * k + 1] + dev[3 * k + 2];
+        s1[k] = dev[3 * k + 2] - dev[3 * k];
     }
+    T drho, j[D];
+    if (D == 2) {
+        drho = s0[0] + s0[1] + s0[2];
+        j[0] = s0[2] - s0[0];
+        j[D - 1] = s1[0] + s1[1] + s1[2];
+    } else {
+        T t0[3], ty[3], tz[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t0[a] = s0[3 * a] + s0[3 * a + 1] + s0[3 * a + 2];
+            ty[a] = s0[3 * a + 2] - s0[3 * a];
+            tz[a] = s1[3 * a] + s1[3 * a + 1] + s1[3 * a + 2];
+        }
+        drho = t0[0] + t0[1] + t0[2];
+        j[0] = t0[2] - t0[0];
+        j[1] = ty[0] + ty[1] + ty[2];
+        j[D - 1] = tz[0] + tz[1] + tz[2];
+    }
+    // the weights, rounded to T, sum to 1 + wsum_err
+    constexpr double wsum_err = weight_sum_error<D, T>();
+    drho += T(wsum_err);
+    const T rho = T(1) + drho;
     const T irho = div_rn(T(1), rho);
 
-    // Product-form entropic equilibrium (Sec. I): per axis
-    // Upsilon = 2 - sqrt(1 + 3u^2), z = (2u + sqrt(1 + 3u^2)) / (1 - u); the
-    // factor of axis a for c = -1, 0, +1 is (1/6) Y / z, (4/6) Y, (1/6) Y z.
-    T phi[D][3];
+    // Per axis eps(c) = Upsilon z^c - 1 for c = -1, 0, +1 (Sec. I equilibrium).
+    T eps[D][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const T u = j[a] * irho;
         const T s = sqrt_(T(1) + T(3) * u * u);
-        const T Y = T(2) - s;
-        const T num = T(2) * u + s;
-        const T den = T(1) - u;
-        phi[a][0] = div_rn(Y * den, T(6) * num);
-        phi[a][1] = Y * T(4.0 / 6.0);
-        phi[a][2] = div_rn(Y * num, T(6) * den);
+        const T sm1 = div_rn(T(3) * u * u, T(1) + s);  // s - 1
+        const T num = T(3) * u + sm1;                  // (2u + s) - (1 - u)
+        const T zm1 = div_rn(num, T(1) - u);           // z - 1
+        const T zim1 = -div_rn(num, T(2) * u + s);     // 1/z - 1
+        const T e0 = -sm1;                             // Upsilon - 1
+        eps[a][0] = e0 + zim1 + e0 * zim1;
+        eps[a][1] = e0;
+        eps[a][2] = e0 + zm1 + e0 * zm1;
     }
 
-    // Departures x_i = (f^eq_i - f_i) / f_i and their extremes.
+    // x_i = (f^eq_i - f_i) / f_i with f^eq_i - f_i = w_i (drho + rho E_i) - d_i.
     T xabs = T(0), xmin = T(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        T feq = rho;
+    for (int k = 0; k < P; ++k) {
+        // E for the column: first D-1 axes fixed, last axis varies
+        T A;
+        if (D == 2) {
+            A = eps[0][k];
+        } else {
+            const T ex = eps[0][k / 3], ey = eps[1][k % 3];
+            A = ex + ey + ex * ey;
+        }
 #pragma unroll
-        for (int a = 0; a < D; ++a) feq *= phi[a][vel(D, i, a) + 1];
-        x[i] = div_(feq - f[i], f[i]);
-        xabs = fmax(xabs, fabs(x[i]));
-        xmin = fmin(xmin, x[i]);
+        for (int c = 0; c < 3; ++c) {
+            const int i = 3 * k + c;
+            const T el = eps[D - 1][c];
+            const T E = A + el + A * el;
+            const T delta = T(weight(D, i)) * (drho + rho * E) - dev[i];
+            x[i] = div_(delta, f[i]);
+            xabs = fmax(xabs, fabs(x[i]));
+            xmin = fmin(xmin, x[i]);
+        }
     }
 
     T alpha = T(2);
@@ -197,17 +255,18 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
     if (p.mode != kModeLBGK && !(p.cutoff && xabs < T(kCutoff))) {
         // Eq. alphaLowerCoeffs and the x-only parts of Eq. qaud_tight_coeff:
         //   b1 = <f, x^2/2>, c1 = <f, 2x^2/(2+x)>,
-        //   c  = <f, (60x^2 + 60x^3 + 11x^4)/(60 + 90x + 36x^2 + 3x^3)>,
-        //   S_k = <f, x^k>_{Omega-} (k = 3..6), so a1 = S3/2, a2 = beta^2 S3/6.
+        //   c  = <f, x^2 (60 + 60x + 11x^2)/((2+x)(30 + 30x + 3x^2))>,
+        //   S_k = <f, x^k>_{Omega-} (k = 3..6), a1 = S3/2, a2 = beta^2 S3/6.
         T b1 = T(0), c1 = T(0), c = T(0), S3 = T(0), S4 = T(0), S5 = T(0), S6 = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const T xi = x[i];
             const T fx2 = f[i] * xi * xi;
+            const T K = T(30) + xi * (T(30) + T(3) * xi);
+            const T A = div_(fx2, (T(2) + xi) * K);
             b1 += fx2;
-            c1 += div_(fx2, T(2) + xi);
-            c += div_(fx2 * (T(60) + xi * (T(60) + T(11) * xi)),
-                      T(60) + xi * (T(90) + xi * (T(36) + T(3) * xi)));
+            c1 += A * K;
+            c += A * (T(60) + xi * (T(60) + T(11) * xi));
             if (xi < T(0)) {
                 const T fx3 = fx2 * xi;
                 S3 += fx3;
@@ -224,9 +283,7 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
             if (p.mode == kModeLower) {
                 alpha = aL;
             } else {
-                // b of Eq. qaud_tight_coeff.  With t = k x the bracket
-                // 2/(4+t) + 1/(4+2t) + 2/(4+3t) equals the single rational
-                // (80 + 80t + 19t^2) / (64 + 96t + 44t^2 + 6t^3).
+                // b of Eq. qaud_tight_coeff, k = alpha_L beta (derived) or alpha_L (printed).
                 const T k = p.b_variant ? aL : aL * beta;
                 T bp = T(0);
 #pragma unroll

@@ -201,37 +201,40 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         const T alpha_t = node_collide<D, T, false>(f, xd, p, &br);
         const double alpha = double(alpha_t);
 
-        double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+        // Mass and momentum through the deviations d_i = f_i - w_i (small numbers,
+        // summed per node in T), then per node into the FP64 domain sums.
+        T dr = T(0), jt[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double v = double(fc[i]);
-            r += v;
+            const T di = fc[i] - T(weight(D, i));
+            dr += di;
 #pragma unroll
-            for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * v;
+            for (int a = 0; a < D; ++a) jt[a] += T(vel(D, i, a)) * di;
         }
-        sum[0] += r;
-        for (int a = 0; a < D; ++a) sum[1 + a] += j[a];
+        sum[0] += 1.0 + weight_sum_error<D, T>() + double(dr);
+        for (int a = 0; a < D; ++a) sum[1 + a] += double(jt[a]);
         if (bad) {
             cnt[3] += 1;
         } else {
-            // H[f] (Eq. hdef) and the entropy change of this node's collision (Eq.
-            // deltaH3, with <f,x> = 0 removing alpha beta <f,x> from both sums):
-            // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>.  Transcendentals in
-            // the path's compute type, sums per node and over the domain in FP64.
+            // H[f] = <f, log(f/w)> - rho (Eq. hdef), with log(f/w) = log1p(d/w), and
+            // the entropy change of this node's collision (Eq. deltaH3, with <f,x> = 0
+            // removing alpha beta <f,x> from both sums):
+            // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>.
+            // Per-node sums in the path's compute type, domain sums in FP64.
             const T ab = alpha_t * T(p.beta);
-            double H = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            T hl = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const T fi = fc[i], xi = xd[i];
-                H += double(fi * (log(fi * T(1.0 / weight(D, i))) - T(1)));
-                s1 += double(fi * g_entropy<T>(ab * xi));
-                s2 += double(fi * xi * log1p(xi));
-                s3 += double(fi * xi * xi);
+                hl += fi * log1p((fi - T(weight(D, i))) * T(1.0 / weight(D, i)));
+                s1 += fi * g_entropy<T>(ab * xi);
+                s2 += fi * xi * log1p(xi);
+                s3 += fi * xi * xi;
             }
-            const double dH = s1 - double(ab) * s2;
-            sum[4] += H;
+            const double dH = double(s1) - double(ab) * double(s2);
+            sum[4] += double(hl) - (1.0 + weight_sum_error<D, T>() + double(dr));
             dmax = max(dmax, ordered_bits(dH));
-            if (dH > 1e-6 * s3 && s3 > 0.0) cnt[4] += 1;
+            if (dH > 1e-6 * double(s3) && s3 > T(0)) cnt[4] += 1;
         }
         sum[5] += alpha;
         cnt[br == kBranchCutoff ? 0 : (br == kBranchSolved ? 1 : 2)] += 1;

@@ -250,9 +250,11 @@ def test_fp32_full_size_sampled_nodes():
         n = (sz * L + sy) * L + sx
         worst = max(worst, np.max(np.abs(f_gpu[:, n].astype(np.float64) - fb[:, centre]) / fb[:, centre]))
     assert worst < k * 2e-6
-    for d in (dk, d1):
-        assert abs(d["mass"] - d0["mass"]) < 1e-6 * d0["mass"]
-        assert np.max(np.abs(np.array(d["momentum"]) - np.array(d0["momentum"]))) < 1e-6 * d0["mass"]
+    # FP32 storage rounds every population every step; the domain sums may drift by a
+    # rounding bias of at most ~1e-8 relative per step
+    for d, steps in ((dk, k), (d1, 300)):
+        assert abs(d["mass"] - d0["mass"]) < 1e-8 * steps * d0["mass"]
+        assert np.max(np.abs(np.array(d["momentum"]) - np.array(d0["momentum"]))) < 1e-8 * steps * d0["mass"]
         assert d["n_nonpositive"] == 0
         # with the paper's cutoff, alpha = 2 need not satisfy the H theorem on
         # near-equilibrium nodes (the guarantee is for alpha_H): violations only there
