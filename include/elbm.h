@@ -84,6 +84,17 @@ extern "C" {
 #define ELBM_B_DERIVED 0
 #define ELBM_B_PRINTED 1
 
+/* Kernel of elbm_step.  DIRECT: one node per thread, neighbours loaded
+ * through the L1 cache; any dims.  ROWS: persistent CTAs stage every source
+ * row of an x-row in shared memory with bulk asynchronous copies (TMA engine,
+ * mbarrier pipeline); needs FP32 or 16-bit storage, nx * element size a
+ * multiple of 16 bytes and nx <= 1024 (D2Q9) or 512 (D3Q27).  AUTO (default)
+ * takes ROWS when it applies, else DIRECT.  Both kernels evaluate the same
+ * arithmetic in the same order, so their results are bitwise identical. */
+#define ELBM_KERNEL_AUTO 0
+#define ELBM_KERNEL_DIRECT 1
+#define ELBM_KERNEL_ROWS 2
+
 /* Location of a caller buffer. */
 #define ELBM_MEM_DEVICE 0
 #define ELBM_MEM_HOST 1
@@ -106,6 +117,7 @@ typedef struct elbm_opts {
     int device;     /* CUDA device ordinal, default 0                                */
     double rho0;    /* reference density of deviation storage, default 1.0           */
     void *stream;   /* cudaStream_t for all work; NULL = the legacy default stream   */
+    int kernel;     /* ELBM_KERNEL_*, default ELBM_KERNEL_AUTO                       */
 } elbm_opts;
 
 /* Domain-wide diagnostics of the current state and of the collision that the
@@ -177,7 +189,10 @@ int elbm_init_equilibrium(elbm_t *h, const double *rho, const double *u, int whe
 
 /* Advances the state by n >= 0 time steps (one fused pull-stream + collide
  * kernel launch per step, ping-pong between the two buffers).  Asynchronous.
- * Errors: ELBM_ERR_ARG (n < 0), ELBM_ERR_CUDA (launch failure). */
+ * Errors: ELBM_ERR_ARG (n < 0), ELBM_ERR_UNSUPPORTED (opts.kernel ==
+ * ELBM_KERNEL_ROWS where it does not apply), ELBM_ERR_CUDA (launch failure).
+ * A bounded device-side wait of the ROWS kernel that expires is reported as
+ * ELBM_ERR_TIMEOUT by the next synchronising call. */
 int elbm_step(elbm_t *h, int64_t n);
 
 /* rho and u of the current (post-collision) state at every node, computed in
@@ -210,7 +225,8 @@ int elbm_set_populations(elbm_t *h, const void *src, int where);
 int elbm_step_count(const elbm_t *h, int64_t *steps);
 
 /* Waits for all work enqueued on the handle's stream; reports deferred
- * device errors as ELBM_ERR_CUDA. */
+ * device errors as ELBM_ERR_CUDA and an expired device-side wait as
+ * ELBM_ERR_TIMEOUT (the flag is cleared when reported). */
 int elbm_synchronize(elbm_t *h);
 
 #ifdef __cplusplus

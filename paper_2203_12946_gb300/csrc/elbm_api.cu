@@ -30,6 +30,7 @@ struct elbm {
     double *stage = nullptr;
     size_t stage_bytes = 0;
     DiagAcc *acc = nullptr;
+    int *err_word = nullptr; // device: ELBM_ERR_TIMEOUT when a bounded device wait expired
     int num_sms = 0;
     int64_t steps = 0;
     std::string err;
@@ -128,6 +129,20 @@ int ensure_stage(elbm_t *h, size_t bytes)
     return ELBM_OK;
 }
 
+// Reads (and clears) the device error word after the stream has been
+// synchronised; returns ELBM_ERR_TIMEOUT when a bounded device wait expired.
+int check_device_flag(elbm_t *h, const char *what)
+{
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, h->err_word, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    if (flag != 0) {
+        cudaMemset(h->err_word, 0, sizeof(int));
+        return fail(h, ELBM_ERR_TIMEOUT, "%s: a bounded device-side wait expired (the step was not completed)", what);
+    }
+    return ELBM_OK;
+}
+
 #define ELBM_BY_LATTICE(h, FN, ...)                                                               \
     ((h)->D == 2 ? eelbm::FN##_d2q9(__VA_ARGS__) : eelbm::FN##_d3q27(__VA_ARGS__))
 
@@ -145,6 +160,7 @@ void elbm_default_opts(elbm_opts *o)
     o->device = 0;
     o->rho0 = 1.0;
     o->stream = nullptr;
+    o->kernel = ELBM_KERNEL_AUTO;
 }
 
 int elbm_population_bytes(int lattice, const int64_t dims[3], int storage, size_t *bytes)
@@ -193,6 +209,8 @@ int elbm_create(elbm_t **out, int lattice, const int64_t dims[3], double beta, i
         return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown b_variant %d", o.b_variant);
     if (o.cutoff != 0 && o.cutoff != 1) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: cutoff must be 0 or 1");
     if (!(o.rho0 > 0.0)) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: rho0 must be positive");
+    if (o.kernel < ELBM_KERNEL_AUTO || o.kernel > ELBM_KERNEL_ROWS)
+        return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown kernel %d", o.kernel);
     size_t bytes = 0;
     int st = elbm_population_bytes(lattice, dims, o.storage, &bytes);
     if (st != ELBM_OK) return st;
@@ -226,9 +244,26 @@ int elbm_create(elbm_t **out, int lattice, const int64_t dims[3], double beta, i
         return cuda_fail(nullptr, e, "elbm_create: cudaDeviceGetAttribute");
     }
     e = cudaMalloc(reinterpret_cast<void **>(&h->acc), sizeof(DiagAcc));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&h->err_word), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->err_word, 0, sizeof(int));
     if (e != cudaSuccess) {
+        cudaFree(h->acc);
+        cudaFree(h->err_word);
         delete h;
-        return cuda_fail(nullptr, e, "elbm_create: cudaMalloc(diagnostics scratch)");
+        return cuda_fail(nullptr, e, "elbm_create: cudaMalloc(scratch)");
+    }
+    if (o.kernel == ELBM_KERNEL_ROWS) {
+        const bool ok = lattice == ELBM_D2Q9 ? eelbm::rows_kernel_applies_d2q9(o.storage, h->g)
+                                             : eelbm::rows_kernel_applies_d3q27(o.storage, h->g);
+        if (!ok) {
+            cudaFree(h->acc);
+            cudaFree(h->err_word);
+            delete h;
+            return fail(nullptr, ELBM_ERR_UNSUPPORTED,
+                        "elbm_create: the ROWS kernel needs FP32/16-bit storage, nx * element size a multiple "
+                        "of 16 bytes and nx <= %d",
+                        lattice == ELBM_D2Q9 ? 1024 : 512);
+        }
     }
     *out = h;
     return ELBM_OK;
@@ -246,6 +281,7 @@ void elbm_destroy(elbm_t *h)
     }
     cudaFree(h->stage);
     cudaFree(h->acc);
+    cudaFree(h->err_word);
     delete h;
 }
 
@@ -336,7 +372,7 @@ int elbm_step(elbm_t *h, int64_t n)
     const CollideParams p = params_of(h);
     for (int64_t k = 0; k < n; ++k) {
         cudaError_t e = ELBM_BY_LATTICE(h, launch_step, h->opts.storage, h->pop[h->cur], h->pop[h->cur ^ 1], h->g, p,
-                                        h->stream);
+                                        h->opts.kernel, h->num_sms, h->err_word, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "elbm_step: kernel launch");
         h->cur ^= 1;
         h->steps += 1;
@@ -374,6 +410,7 @@ int elbm_moments(elbm_t *h, double *rho_out, double *u_out, int where)
         }
         e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: synchronize");
+        return check_device_flag(h, "elbm_moments");
     }
     return ELBM_OK;
 }
@@ -427,6 +464,8 @@ int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist)
     e = cudaMemcpyAsync(&acc, h->acc, sizeof acc, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: read back");
+    int st = check_device_flag(h, "elbm_diagnostics");
+    if (st != ELBM_OK) return st;
     const int64_t N = h->g.N;
     out->mass = acc.sum[0];
     out->momentum[0] = acc.sum[1];
@@ -464,6 +503,7 @@ int elbm_get_populations(elbm_t *h, void *dst, int where)
                                     h->stream);
     if (e == cudaSuccess && where == ELBM_MEM_HOST) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "elbm_get_populations");
+    if (where == ELBM_MEM_HOST) return check_device_flag(h, "elbm_get_populations");
     return ELBM_OK;
 }
 
@@ -499,7 +539,7 @@ int elbm_synchronize(elbm_t *h)
     DeviceGuard guard(h->opts.device);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "elbm_synchronize");
-    return ELBM_OK;
+    return check_device_flag(h, "elbm_synchronize");
 }
 
 } // extern "C"

@@ -86,12 +86,14 @@ __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 struct StoreF64 {
     using S = double;
     using T = double;
+    static constexpr int kRows = 0; // row-staged kernel not instantiated (FP64 is the parity path)
     __device__ static __forceinline__ T load(S s, T, T) { return s; }
     __device__ static __forceinline__ S store(T f, T, T) { return f; }
     __device__ static __forceinline__ double load64(S s, double, double) { return s; }
     __device__ static __forceinline__ S store64(double f, double, double) { return f; }
 };
 struct StoreF32 {
+    static constexpr int kRows = 1;
     using S = float;
     using T = float;
     __device__ static __forceinline__ T load(S s, T, T) { return s; }
@@ -100,6 +102,7 @@ struct StoreF32 {
     __device__ static __forceinline__ S store64(double f, double, double) { return float(f); }
 };
 struct StoreF16Dev {
+    static constexpr int kRows = 1;
     using S = __half;
     using T = float;
     __device__ static __forceinline__ T load(S s, T w, T rho0) { return fmaf(w, rho0, __half2float(s)); }
@@ -114,6 +117,7 @@ struct StoreF16Dev {
     }
 };
 struct StoreBF16Dev {
+    static constexpr int kRows = 1;
     using S = __nv_bfloat16;
     using T = float;
     __device__ static __forceinline__ T load(S s, T w, T rho0) { return fmaf(w, rho0, __bfloat162float(s)); }
@@ -204,9 +208,9 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
         j[1] = ty[0] + ty[1] + ty[2];
         j[D - 1] = tz[0] + tz[1] + tz[2];
     }
-    // the weights, rounded to T, sum to 1 + wsum_err
-    constexpr double wsum_err = weight_sum_error<D, T>();
-    drho += T(wsum_err);
+    // rho = 1 + drho.  The weights rounded to T sum to 1 + e_w (|e_w| ~ 1e-8 in
+    // FP32); building f^eq on those same weights with 1 + drho gives it the mass
+    // (1 + drho)(1 + e_w) = sum f + drho e_w, so e_w must not be added to drho.
     const T rho = T(1) + drho;
     const T irho = div_rn(T(1), rho);
 

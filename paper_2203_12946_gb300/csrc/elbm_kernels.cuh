@@ -15,6 +15,7 @@
 
 #include "elbm_device.cuh"
 #include "elbm_launch.h"
+#include "elbm_tma.cuh"
 
 namespace eelbm {
 namespace ELBM_SUFFIX {
@@ -307,12 +308,92 @@ static inline unsigned blocks_for(int64_t N, int block) { return unsigned((N + b
 #define ELBM_CAT2(a, b) a##_##b
 #define ELBM_CAT(a, b) ELBM_CAT2(a, b)
 
+namespace ELBM_SUFFIX {
+
+// Row-staged instantiations: (NXMAX, stages) per storage element size.
+constexpr int kRowThreads = 256;
+template <class S>
+constexpr int row_stages()
+{
+    return sizeof(S) >= 4 ? (D == 3 ? 3 : 3) : 5;
+}
+
+template <class ST, int NXMAX>
+cudaError_t launch_rows(const void *fin, void *fout, const Geometry &g, const CollideParams &p, int num_sms,
+                        int *err, cudaStream_t s)
+{
+    using S = typename ST::S;
+    constexpr int STAGES = (D == 3 && NXMAX > 256) ? 2 : row_stages<S>();
+    constexpr size_t smem = rows_smem_bytes<Q, S, NXMAX, STAGES>();
+    auto kern = k_step_rows<D, ST, NXMAX, kRowThreads, STAGES>;
+    // one-time set-up per instantiation (single-device library use)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kRowThreads, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = n < 1 ? 1 : n;
+    }
+    const int rows = g.ny * g.nz;
+    int grid = per_sm * (num_sms > 0 ? num_sms : 1);
+    if (grid > rows) grid = rows;
+    kern<<<grid, kRowThreads, smem, s>>>(static_cast<const S *>(fin), static_cast<S *>(fout), g, p, err);
+    return cudaGetLastError();
+}
+
+template <class ST>
+int rows_nxmax(const Geometry &g)
+{
+    using S = typename ST::S;
+    if (ST::kRows == 0) return 0;
+    if ((size_t(g.nx) * sizeof(S)) % 16 != 0) return 0;
+    const int cands[3] = {D == 3 ? 128 : 256, D == 3 ? 256 : 1024, D == 3 ? 512 : 0};
+    for (int c : cands)
+        if (c && g.nx <= c) return c;
+    return 0;
+}
+
+} // namespace ELBM_SUFFIX
+
+bool ELBM_CAT(rows_kernel_applies, ELBM_SUFFIX)(int storage, const Geometry &g)
+{
+    using namespace ELBM_SUFFIX;
+    switch (storage) {
+    case ELBM_STORE_F32: return rows_nxmax<StoreF32>(g) > 0;
+    case ELBM_STORE_F16DEV: return rows_nxmax<StoreF16Dev>(g) > 0;
+    case ELBM_STORE_BF16DEV: return rows_nxmax<StoreBF16Dev>(g) > 0;
+    default: return false;
+    }
+}
+
 cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, void *fout,
-                                               const Geometry &g, const CollideParams &p,
-                                               cudaStream_t s)
+                                               const Geometry &g, const CollideParams &p, int kernel,
+                                               int num_sms, int *err, cudaStream_t s)
 {
     using namespace ELBM_SUFFIX;
     if (g.N == 0) return cudaSuccess;
+    if (kernel != ELBM_KERNEL_DIRECT && ELBM_CAT(rows_kernel_applies, ELBM_SUFFIX)(storage, g)) {
+        // the row pipeline is only instantiated for the FP32 and 16-bit storages
+#define ELBM_ROWS_FOR(STT)                                                                        \
+    {                                                                                             \
+        const int nm = rows_nxmax<STT>(g);                                                        \
+        if (nm == (D == 3 ? 128 : 256))                                                           \
+            return launch_rows<STT, (D == 3 ? 128 : 256)>(fin, fout, g, p, num_sms, err, s);      \
+        if (nm == (D == 3 ? 256 : 1024))                                                          \
+            return launch_rows<STT, (D == 3 ? 256 : 1024)>(fin, fout, g, p, num_sms, err, s);     \
+        if (D == 3 && nm == 512) return launch_rows<STT, 512>(fin, fout, g, p, num_sms, err, s);  \
+    }
+        switch (storage) {
+        case ELBM_STORE_F32: ELBM_ROWS_FOR(StoreF32) break;
+        case ELBM_STORE_F16DEV: ELBM_ROWS_FOR(StoreF16Dev) break;
+        case ELBM_STORE_BF16DEV: ELBM_ROWS_FOR(StoreBF16Dev) break;
+        default: break;
+        }
+#undef ELBM_ROWS_FOR
+    }
+    if (kernel == ELBM_KERNEL_ROWS) return cudaErrorNotSupported;
     ELBM_STORAGE_SWITCH(storage,
                         (k_step<ST><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
                             static_cast<const typename ST::S *>(fin), static_cast<typename ST::S *>(fout),

@@ -41,7 +41,9 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
 
 #define ELBM_DECLARE_LAUNCHERS(SUFFIX)                                                               \
     cudaError_t launch_step_##SUFFIX(int storage, const void *fin, void *fout, const Geometry &g,   \
-                                     const CollideParams &p, cudaStream_t s);                        \
+                                     const CollideParams &p, int kernel, int num_sms, int *err,      \
+                                     cudaStream_t s);                                                \
+    bool rows_kernel_applies_##SUFFIX(int storage, const Geometry &g);                               \
     cudaError_t launch_init_##SUFFIX(int storage, const double *rho, const double *u, void *f,      \
                                      const Geometry &g, double rho_uniform, double rho0,             \
                                      cudaStream_t s);                                                \

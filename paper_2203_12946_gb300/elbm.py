@@ -33,6 +33,7 @@ ELBM_STORE_F64, ELBM_STORE_F32, ELBM_STORE_F16DEV, ELBM_STORE_BF16DEV = 0, 1, 2,
 ELBM_ALPHA_HIGHER, ELBM_ALPHA_LOWER, ELBM_ALPHA_LBGK = 0, 1, 2
 ELBM_B_DERIVED, ELBM_B_PRINTED = 0, 1
 ELBM_MEM_DEVICE, ELBM_MEM_HOST = 0, 1
+ELBM_KERNEL_AUTO, ELBM_KERNEL_DIRECT, ELBM_KERNEL_ROWS = 0, 1, 2
 ELBM_BRANCH_CUTOFF, ELBM_BRANCH_SOLVED, ELBM_BRANCH_CLAMPED = 0, 1, 2
 ELBM_HIST_BINS = 256
 
@@ -49,7 +50,7 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
 class elbm_opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("alpha_mode", ctypes.c_int), ("cutoff", ctypes.c_int),
                 ("b_variant", ctypes.c_int), ("device", ctypes.c_int), ("rho0", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int)]
 
 
 class elbm_diag(ctypes.Structure):
@@ -249,7 +250,8 @@ class Simulation:
     """
 
     def __init__(self, lattice, dims, beta, storage="f32", alpha_mode=ELBM_ALPHA_HIGHER,
-                 cutoff=True, b_variant=ELBM_B_DERIVED, device=0, rho0=1.0, stream=None):
+                 cutoff=True, b_variant=ELBM_B_DERIVED, device=0, rho0=1.0, stream=None,
+                 kernel=ELBM_KERNEL_AUTO):
         import torch
 
         if not torch.cuda.is_available():
@@ -270,6 +272,7 @@ class Simulation:
         o.b_variant = int(b_variant)
         o.device = int(device)
         o.rho0 = float(rho0)
+        o.kernel = int(kernel)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         o.stream = self.stream.cuda_stream
         self.h = elbm_create(self.lattice, self.dims, beta, ELBM_BC_PERIODIC, o)

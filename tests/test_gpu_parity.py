@@ -55,6 +55,7 @@ def gpu_run(D, dims, beta, f0, nsteps, storage="f64", **kw):
         sim.set_populations(f0)
         sim.step(nsteps)
         f = sim.get_populations().astype(np.float64)
+        sim.synchronize()  # also reports an expired device-side wait
     return f
 
 
@@ -436,3 +437,39 @@ def _opts(storage):
     o = E.elbm_default_opts()
     o.storage = storage
     return o
+
+
+# ---------------------------------------------------------------------------
+# the two step kernels (DIRECT: L1 gathers; ROWS: bulk-async row staging)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,dims,storage", [
+    (3, (32, 20, 12), "f32"), (3, (256, 6, 5), "f32"), (3, (512, 3, 2), "f32"), (3, (100, 7, 9), "f32"),
+    (2, (1024, 24, 1), "f32"), (2, (300, 37, 1), "f32"), (2, (8, 3, 1), "f32"),
+    (2, (64, 64, 1), "f16dev"), (3, (64, 16, 8), "bf16dev"), (3, (48, 5, 7), "f16dev"),
+])
+def test_rows_kernel_matches_direct_bitwise(D, dims, storage):
+    """Both kernels run node_collide on the same inputs in the same order: identical bits."""
+    f0 = noisy_state(D, dims, 5e-3, seed=43)
+    c, w = O.lattice(D)
+    outs = []
+    for kern in (E.ELBM_KERNEL_DIRECT, E.ELBM_KERNEL_ROWS):
+        with E.Simulation(LAT[D], dims, 0.999, storage=storage, kernel=kern) as sim:
+            if storage == "f32":
+                sim.set_populations(f0.astype(np.float32))
+            else:
+                rho, u = O.moments_field(D, f0)
+                sim.init_equilibrium(rho, u)
+            sim.step(6)
+            outs.append(sim.get_populations())
+            sim.synchronize()
+    assert outs[0].dtype == outs[1].dtype
+    assert np.array_equal(outs[0].view(np.uint8), outs[1].view(np.uint8))
+
+
+@pytest.mark.parametrize("D,dims,storage", [(2, (37, 8, 1), "f32"), (3, (30, 4, 4), "f32"),
+                                            (2, (64, 8, 1), "f64"), (3, (1028, 2, 2), "f32")])
+def test_rows_kernel_rejected_where_it_does_not_apply(D, dims, storage):
+    with pytest.raises(E.ElbmError) as ei:
+        E.Simulation(LAT[D], dims, 0.9, storage=storage, kernel=E.ELBM_KERNEL_ROWS)
+    assert ei.value.code == E.ELBM_ERR_UNSUPPORTED
