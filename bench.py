@@ -38,7 +38,6 @@ U0 = 0.05
 LATTICE_Q = 27
 DIAG_EVERY = 100
 STORAGE = "f32"
-BYTES_PER_NODE = 2 * LATTICE_Q * 4  # read Q + write Q FP32 populations
 WORKLOAD = "D3Q27 256^3 periodic Taylor-Green vortex, u0=0.05, beta=0.999, FP32 SoA ping-pong"
 METRIC = "MLUPS (D3Q27 256^3 FP32 entropic LBM step)"
 PROFILE = os.path.join(ROOT, "profiles", "k_step_d3q27_f32_tgv256.md")
@@ -281,7 +280,9 @@ def run_gpu(args):
     u_d = u_h.to(dev)
 
     stream = torch.cuda.current_stream(dev)
-    sim = E.Simulation(E.ELBM_D3Q27, dims, BETA, storage=STORAGE, device=local, stream=stream)
+    kernel = {"auto": E.ELBM_KERNEL_AUTO, "direct": E.ELBM_KERNEL_DIRECT, "rows": E.ELBM_KERNEL_ROWS}[args.kernel]
+    sim = E.Simulation(E.ELBM_D3Q27, dims, BETA, storage=args.storage, device=local, stream=stream,
+                       kernel=kernel)
     sim.init_equilibrium(rho_d, u_d)
 
     def barrier():
@@ -344,21 +345,26 @@ def run_gpu(args):
     d2h = (rho_out.numel() + u_out.numel()) * 8
 
     peak, peak_src = measured_peaks()
-    achieved = BYTES_PER_NODE * N / kern_avg / 1e9
-    traffic = profiled_traffic()
+    elem = {"f32": 4, "f16dev": 2, "bf16dev": 2}[args.storage]
+    bytes_per_node = 2 * LATTICE_Q * elem
+    rows_ok = (L * elem) % 16 == 0 and L <= 512  # the ROWS kernel applies (see elbm.h)
+    kname = ("k_step_rows" if (args.kernel == "rows" or (args.kernel == "auto" and rows_ok))
+             else "k_step") + f"<{args.storage}> (D3Q27)"
+    achieved = bytes_per_node * N / kern_avg / 1e9
+    traffic = profiled_traffic() if (args.storage == STORAGE and args.kernel == "auto") else None
     value = aggregate_mlups(N, args.steps, world, elapsed)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": "D3Q27", "dims": [L, L, L], "beta": BETA,
-                   "u0": U0, "storage": STORAGE, "diag_every": DIAG_EVERY,
+                   "u0": U0, "storage": args.storage, "diag_every": DIAG_EVERY,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (two 1.81 GB population buffers)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "k_step<StoreF32> (D3Q27)",
-                     "algorithmic_bytes_per_launch": BYTES_PER_NODE * N,
+                     "kernel": kname,
+                     "algorithmic_bytes_per_launch": bytes_per_node * N,
                      "kernel_ms_avg": 1e3 * kern_avg},
         "e2e": {"value": aggregate_mlups(N, args.steps, world, e2e_t), "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
@@ -389,6 +395,8 @@ def main():
     ap.add_argument("--cpu-slab", type=int, default=32)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["auto", "direct", "rows"], default="auto")
+    ap.add_argument("--storage", choices=["f32", "f16dev", "bf16dev"], default=STORAGE)
     ap.add_argument("--L", type=int, default=L, help="domain side (profiling runs only; "
                     "the benchmark workload is 256)")
     args = ap.parse_args()
