@@ -90,7 +90,8 @@ extern "C" {
  * mbarrier pipeline); needs FP32 or 16-bit storage, nx * element size a
  * multiple of 16 bytes and nx <= 1024 (D2Q9) or 512 (D3Q27).  AUTO (default)
  * takes ROWS when it applies, else DIRECT.  Both kernels evaluate the same
- * arithmetic in the same order, so their results are bitwise identical. */
+ * per-node arithmetic; they agree to rounding (the compiler may fuse
+ * multiply-adds differently in each). */
 #define ELBM_KERNEL_AUTO 0
 #define ELBM_KERNEL_DIRECT 1
 #define ELBM_KERNEL_ROWS 2
