@@ -230,6 +230,40 @@ int elbm_step_count(const elbm_t *h, int64_t *steps);
  * ELBM_ERR_TIMEOUT (the flag is cleared when reported). */
 int elbm_synchronize(elbm_t *h);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free diagnostics.  The paper has no counterpart: this is a
+ * service of the library for callers that cannot allocate device memory (an
+ * application whose GPU memory belongs to another allocator or a fixed pool,
+ * code that must not grow its footprint after start-up, a monitoring hook
+ * inside someone else's time step).  elbm_create allocates, so these callers
+ * have no handle; this entry point needs none.
+ *
+ * Computes exactly what elbm_diagnostics computes, for a caller-owned device
+ * buffer `populations` (Q*N elements of opts->storage, the layout above)
+ * holding a post-collision state.  lattice, dims, beta and opts mean what they
+ * mean for elbm_create (opts may be NULL: defaults; only storage, alpha_mode,
+ * cutoff, b_variant, rho0, device and stream are used; opts->device must be
+ * the current device).  *out and alpha_hist (ELBM_HIST_BINS + 2 counts, may be
+ * NULL) are host memory.  Synchronises opts->stream.
+ *
+ * Scratch: the reduction accumulator lives in a file-scope device array of
+ * ELBM_NOALLOC_SCRATCH_BYTES bytes, present on every GPU that loads the
+ * library until the process exits.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  A call whose scratch would exceed that maximum
+ * is rejected with ELBM_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call clears the array
+ * before use, but all calls share it: calls that overlap on the GPU (from
+ * different streams or host threads) race and must be serialised by the
+ * caller.
+ *
+ * Errors (message in elbm_last_error(NULL)): ELBM_ERR_ARG (null pointer,
+ * lattice, dims, beta, options, device not current, scratch too small),
+ * ELBM_ERR_CUDA, ELBM_ERR_NONPHYSICAL (after filling *out). */
+#define ELBM_NOALLOC_SCRATCH_BYTES 4096
+int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], double beta, const elbm_opts *opts,
+                             const void *populations, elbm_diag *out, int64_t *alpha_hist);
+
 #ifdef __cplusplus
 }
 #endif

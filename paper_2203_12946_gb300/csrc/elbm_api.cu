@@ -148,6 +148,8 @@ int check_device_flag(elbm_t *h, const char *what)
 
 } // namespace
 
+void eelbm::set_handle_free_error(const char *msg) { g_create_error = msg; }
+
 extern "C" {
 
 void elbm_default_opts(elbm_opts *o)

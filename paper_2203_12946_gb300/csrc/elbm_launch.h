@@ -56,6 +56,9 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
                                      const CollideParams &p, DiagAcc *acc, int num_sms,             \
                                      cudaStream_t s);
 
+// Sets the message returned by elbm_last_error(NULL) (calls without a handle).
+void set_handle_free_error(const char *msg);
+
 ELBM_DECLARE_LAUNCHERS(d2q9)
 ELBM_DECLARE_LAUNCHERS(d3q27)
 

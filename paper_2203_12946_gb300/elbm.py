@@ -44,7 +44,8 @@ STORAGE_BYTES = {ELBM_STORE_F64: 8, ELBM_STORE_F32: 4, ELBM_STORE_F16DEV: 2, ELB
 EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_destroy",
             "elbm_last_error", "elbm_bind_buffers", "elbm_set_stream", "elbm_init_equilibrium",
             "elbm_step", "elbm_moments", "elbm_alpha_field", "elbm_diagnostics",
-            "elbm_get_populations", "elbm_set_populations", "elbm_step_count", "elbm_synchronize"]
+            "elbm_get_populations", "elbm_set_populations", "elbm_step_count", "elbm_synchronize",
+            "elbm_diagnostics_noalloc"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -113,6 +114,9 @@ def load(build_if_missing: bool = True):
             "elbm_set_populations": (ctypes.c_int, [P, P, ctypes.c_int]),
             "elbm_step_count": (ctypes.c_int, [P, ctypes.POINTER(i64)]),
             "elbm_synchronize": (ctypes.c_int, [P]),
+            "elbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(i64), ctypes.c_double,
+                                                        ctypes.POINTER(elbm_opts), P,
+                                                        ctypes.POINTER(elbm_diag), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -214,6 +218,23 @@ def elbm_diagnostics(h, alpha_hist: np.ndarray | None = None, allow_nonphysical:
     code = load().elbm_diagnostics(h, ctypes.byref(d), _ptr(alpha_hist))
     if not (allow_nonphysical and code == ELBM_ERR_NONPHYSICAL):
         _check(h, code, "elbm_diagnostics")
+    out = d.as_dict()
+    out["status"] = code
+    return out
+
+
+def elbm_diagnostics_noalloc(lattice, dims, beta, populations, opts: elbm_opts | None = None,
+                             alpha_hist: np.ndarray | None = None, allow_nonphysical: bool = False) -> dict:
+    """Diagnostics of a caller-owned device population buffer without any device
+    allocation (see include/elbm.h); the first call on a device must precede any
+    stream capture, and overlapping calls must be serialised by the caller."""
+    d = elbm_diag()
+    if opts is None:
+        opts = elbm_default_opts()
+    code = load().elbm_diagnostics_noalloc(int(lattice), _dims(dims), float(beta), ctypes.byref(opts),
+                                           _ptr(populations), ctypes.byref(d), _ptr(alpha_hist))
+    if not (allow_nonphysical and code == ELBM_ERR_NONPHYSICAL):
+        _check(None, code, "elbm_diagnostics_noalloc")
     out = d.as_dict()
     out["status"] = code
     return out
