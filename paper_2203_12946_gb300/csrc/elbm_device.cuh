@@ -68,17 +68,26 @@ struct CollideParams {
 };
 
 // ---------------------------------------------------------------------------
-// Arithmetic helpers.  FP32 divisions on the hot path use the fast reciprocal
-// intrinsic (max error 2 ulp); FP64 uses IEEE division.
+// Arithmetic helpers.  FP32 divisions on the hot path multiply by the
+// approximate reciprocal (rcp.approx.ftz: one MUFU operation, ~1 ulp); every
+// divisor on the path is a normal number of moderate size (populations,
+// 1 + O(x) polynomials), so flushing subnormals changes nothing.  FP64 uses
+// IEEE division.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float rcp_(float b)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+    return r;
+}
+__device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 // FP32 square roots on the path act on 1 + O(u^2) and 1 - 4pq >= 1: the
 // approximate instruction (relative error ~2^-23) loses nothing there.
 __device__ __forceinline__ float sqrt_(float a)
 {
     float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
 }
 // correctly rounded division, for the few divisions whose rounding reaches f^eq
@@ -337,6 +346,221 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
     }
     *branch = br;
     return alpha;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 collision on packed population pairs.
+//
+// The same arithmetic as node_collide<D, float>, evaluated on float2 pairs of
+// populations (2k, 2k+1) with the sm_100-family paired FP32 instructions
+// (__ffma2_rn, __fmul2_rn, __fadd2_rn: two IEEE FP32 operations per
+// instruction).  With Q odd the last pair carries a padding lane (f = 1,
+// x = 0) that contributes nothing to any sum.  The Omega-/Omega+ restricted
+// sums are taken branch-free with min(x,0) / max(x,0): a term of the other set
+// is exactly zero, so the sums equal the restricted ones.
+//   in : fp[NP]  pre-collision populations, pair layout
+//   out: fp[NP]  post-collision populations (when kRelax)
+//        xp[NP]  departures x_i (Eq. xdef), pair layout
+//        returns alpha; *branch receives kBranch*
+// ---------------------------------------------------------------------------
+template <int D>
+struct Pairs {
+    static constexpr int Q = Lattice<D>::Q;
+    static constexpr int NP = (Q + 1) / 2;
+};
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 prcp(float2 a) { return f2(rcp_(a.x), rcp_(a.y)); }
+
+// Weight pair of pair k (0 in the padding lane).
+template <int D>
+__host__ __device__ constexpr float wpair(int k, int lane)
+{
+    return (2 * k + lane) < Lattice<D>::Q ? float(weight(D, 2 * k + lane)) : 0.0f;
+}
+
+template <int D, bool kRelax = true>
+__device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], float2 (&xp)[Pairs<D>::NP],
+                                                    const CollideParams &p, int *branch)
+{
+    constexpr int Q = Lattice<D>::Q;
+    constexpr int NP = Pairs<D>::NP;
+    constexpr bool kPad = (Q % 2) == 1;
+    const float beta = float(p.beta);
+
+    // Deviations d_i = f_i - w_i and the moments (Sec. I), summed along the last
+    // axis first (same grouping as node_collide).
+    float2 dp[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) dp[k] = psub(fp[k], f2(wpair<D>(k, 0), wpair<D>(k, 1)));
+    auto ds = [&](int i) -> float { return (i & 1) ? dp[i >> 1].y : dp[i >> 1].x; };
+    constexpr int P = Q / 3;
+    float s0[P], s1[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        s0[k] = ds(3 * k) + ds(3 * k + 1) + ds(3 * k + 2);
+        s1[k] = ds(3 * k + 2) - ds(3 * k);
+    }
+    float drho, j[D];
+    if (D == 2) {
+        drho = s0[0] + s0[1] + s0[2];
+        j[0] = s0[2] - s0[0];
+        j[D - 1] = s1[0] + s1[1] + s1[2];
+    } else {
+        float t0[3], ty[3], tz[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t0[a] = s0[3 * a] + s0[3 * a + 1] + s0[3 * a + 2];
+            ty[a] = s0[3 * a + 2] - s0[3 * a];
+            tz[a] = s1[3 * a] + s1[3 * a + 1] + s1[3 * a + 2];
+        }
+        drho = t0[0] + t0[1] + t0[2];
+        j[0] = t0[2] - t0[0];
+        j[1] = ty[0] + ty[1] + ty[2];
+        j[D - 1] = tz[0] + tz[1] + tz[2];
+    }
+    const float rho = 1.0f + drho;
+    const float irho = rcp_(rho);
+
+    // Per axis eps(c) = Upsilon z^c - 1 (as in node_collide).
+    float eps[D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float u = j[a] * irho;
+        const float s = sqrt_(1.0f + 3.0f * u * u);
+        const float sm1 = div_(3.0f * u * u, 1.0f + s);
+        const float num = 3.0f * u + sm1;
+        const float zm1 = div_(num, 1.0f - u);
+        const float zim1 = -div_(num, 2.0f * u + s);
+        const float e0 = -sm1;
+        eps[a][0] = e0 + zim1 + e0 * zim1;
+        eps[a][1] = e0;
+        eps[a][2] = e0 + zm1 + e0 * zm1;
+    }
+    // E_i = prod_a (1 + eps_a(c_ia)) - 1, per population.
+    auto E_of = [&](int i) -> float {
+        if (i >= Q) return 0.0f;
+        float A;
+        if (D == 2) {
+            A = eps[0][i / 3];
+        } else {
+            const float ex = eps[0][i / 9], ey = eps[1][(i / 3) % 3];
+            A = ex + ey + ex * ey;
+        }
+        const float el = eps[D - 1][i % 3];
+        return A + el + A * el;
+    };
+
+    // x_i = (f^eq_i - f_i) / f_i with f^eq_i - f_i = w_i (drho + rho E_i) - d_i, and in
+    // the same pass the x-only sums of Eq. alphaLowerCoeffs / qaud_tight_coeff and the
+    // Omega- power sums (wasted only where the whole warp ends on the cutoff branch).
+    float2 xabs2 = f2(0.0f), xmin2 = f2(0.0f);
+    float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f);
+    float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const float2 E = f2(E_of(2 * k), E_of(2 * k + 1));
+        float2 delta = psub(pmul(f2(wpair<D>(k, 0), wpair<D>(k, 1)), pfma(f2(rho), E, f2(drho))), dp[k]);
+        if (kPad && k == NP - 1) delta.y = 0.0f; // padding lane: f = 1, x = 0
+        const float2 xi = pmul(delta, prcp(fp[k]));
+        xp[k] = xi;
+        xabs2 = f2(fmaxf(xabs2.x, fabsf(xi.x)), fmaxf(xabs2.y, fabsf(xi.y)));
+        xmin2 = f2(fminf(xmin2.x, xi.x), fminf(xmin2.y, xi.y));
+        const float2 fx2 = pmul(delta, xi); // f x^2
+        const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
+        const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
+        b1 = padd(b1, fx2);
+        c1 = pfma(A, K, c1);
+        c = pfma(A, pfma(pfma(f2(11.0f), xi, f2(60.0f)), xi, f2(60.0f)), c);
+        const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+        const float2 q = pmul(fx2, xm); // f x^3 on Omega-, 0 elsewhere
+        const float2 xm2 = pmul(xm, xm);
+        S3 = padd(S3, q);
+        S4 = pfma(q, xm, S4);
+        S5 = pfma(q, xm2, S5);
+        S6 = pfma(pmul(q, xm), xm2, S6);
+    }
+    const float xabs = fmaxf(xabs2.x, xabs2.y), xmin = fminf(xmin2.x, xmin2.y);
+
+    float alpha = 2.0f;
+    int br = kBranchCutoff;
+    if (p.mode != kModeLBGK && !(p.cutoff && xabs < float(kCutoff))) {
+        const float sb1 = 0.5f * (b1.x + b1.y), sc1 = 2.0f * (c1.x + c1.y), sc = c.x + c.y;
+        const float s3 = S3.x + S3.y, s4 = S4.x + S4.y, s5 = S5.x + S5.y, s6 = S6.x + S6.y;
+        if (sb1 > 0.0f) {
+            const float aL = quad_root(0.5f * s3, sb1, sc1); // alpha_Lower
+            if (p.mode == kModeLower) {
+                alpha = aL;
+            } else {
+                // b: Omega+ Boole term with k = alpha_L beta (derived) or alpha_L (printed).
+                const float kk = p.b_variant ? aL : aL * beta;
+                float2 bp = f2(0.0f);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const float2 xi = xp[k];
+                    const float2 xq = f2(fmaxf(xi.x, 0.0f), fmaxf(xi.y, 0.0f));
+                    const float2 t = pmul(f2(kk), xq);
+                    const float2 nu = pfma(pfma(f2(19.0f), t, f2(80.0f)), t, f2(80.0f));
+                    const float2 de = pfma(pfma(pfma(f2(6.0f), t, f2(44.0f)), t, f2(96.0f)), t, f2(64.0f));
+                    // f x^3 on Omega+ (0 elsewhere) times the bracket
+                    bp = pfma(pmul(pmul(fp[k], pmul(pmul(xi, xi), xq)), nu), prcp(de), bp);
+                }
+                const float b = sb1 - (2.0f / 15.0f) * aL * beta * beta * (bp.x + bp.y);
+                const float h = quad_root(beta * beta * s3 * (1.0f / 6.0f), b, sc);
+                const float hb = h * beta;
+                const float a = beta * beta *
+                                (s3 * (1.0f / 6.0f) - hb * s4 * (1.0f / 12.0f) + hb * hb * s5 * (1.0f / 20.0f) -
+                                 hb * hb * hb * s6 * (1.0f / 5.0f));
+                alpha = quad_root(a, b, sc); // alpha_Higher
+            }
+            br = kBranchSolved;
+        }
+    }
+    if (p.mode != kModeLBGK && xmin < 0.0f && alpha * beta * (-xmin) > 1.0f) {
+        const float amax = div_(-1.0f, beta * xmin);
+        alpha = 0.5f * (1.0f + amax);
+        if (alpha > amax) alpha = 0.5f * amax;
+        br = kBranchClamped;
+    }
+    if (kRelax) {
+        // f* = f + alpha beta (f^eq - f) with f^eq - f = x f
+        const float2 ab = f2(alpha * beta);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) fp[k] = pfma(pmul(ab, xp[k]), fp[k], fp[k]);
+    }
+    *branch = br;
+    return alpha;
+}
+
+// ---------------------------------------------------------------------------
+// One node's collision on scalar arrays, whatever the compute type: FP32 goes
+// through the packed-pair routine, FP64 through node_collide.
+// ---------------------------------------------------------------------------
+template <int D, class T, bool kRelax = true>
+__device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q], const CollideParams &p,
+                                     int *branch)
+{
+    constexpr int Q = Lattice<D>::Q;
+    if constexpr (sizeof(T) == 4) {
+        constexpr int NP = Pairs<D>::NP;
+        float2 fp[NP], xp[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) fp[k] = make_float2(f[2 * k], (2 * k + 1 < Q) ? f[2 * k + 1] : 1.0f);
+        const float alpha = node_collide_pairs<D, kRelax>(fp, xp, p, branch);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            x[i] = (i & 1) ? xp[i >> 1].y : xp[i >> 1].x;
+            if (kRelax) f[i] = (i & 1) ? fp[i >> 1].y : fp[i >> 1].x;
+        }
+        return alpha;
+    } else {
+        return node_collide<D, T, kRelax>(f, x, p, branch);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -33,21 +33,33 @@ __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x
     y = int(t - (int64_t)z * g.ny);
 }
 
-template <class ST>
+// One node per thread.  Launched either on a 3D grid (x from blockIdx.x,
+// y = blockIdx.y, z = blockIdx.z: no index arithmetic) or, when ny or nz exceed
+// the grid limits, on a 1D grid over all nodes.
+template <class ST, bool kGrid3D>
 __global__ void __launch_bounds__(kStepBlock) k_step(const typename ST::S *__restrict__ fin,
                                                     typename ST::S *__restrict__ fout, Geometry g,
                                                     CollideParams p)
 {
     using T = typename ST::T;
-    const int64_t n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
-    if (n >= g.N) return;
     int x, y, z;
-    node_coords(n, g, x, y, z);
+    int64_t n;
+    if (kGrid3D) {
+        x = int(blockIdx.x) * kStepBlock + int(threadIdx.x);
+        if (x >= g.nx) return;
+        y = int(blockIdx.y);
+        z = int(blockIdx.z);
+        n = ((int64_t)z * g.ny + y) * g.nx + x;
+    } else {
+        n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
+        if (n >= g.N) return;
+        node_coords(n, g, x, y, z);
+    }
     T f[Q], xd[Q];
     const T rho0 = T(p.rho0);
     pull_load<D, ST>(fin, g, x, y, z, rho0, f);
     int br;
-    node_collide<D, T, true>(f, xd, p, &br);
+    collide<D, T, true>(f, xd, p, &br);
 #pragma unroll
     for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
 }
@@ -127,7 +139,7 @@ __global__ void __launch_bounds__(kStepBlock) k_alpha(const typename ST::S *__re
     T f[Q], xd[Q];
     pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
     int br;
-    const T alpha = node_collide<D, T, false>(f, xd, p, &br);
+    const T alpha = collide<D, T, false>(f, xd, p, &br);
     alpha_out[n] = double(alpha);
     if (flags) flags[n] = uint8_t(br);
 }
@@ -199,7 +211,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
             bad |= !(f[i] > T(0)) || !isfinite(f[i]);
         }
         int br;
-        const T alpha_t = node_collide<D, T, false>(f, xd, p, &br);
+        const T alpha_t = collide<D, T, false>(f, xd, p, &br);
         const double alpha = double(alpha_t);
 
         // Mass and momentum through the deviations d_i = f_i - w_i (small numbers,
@@ -394,10 +406,16 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
 #undef ELBM_ROWS_FOR
     }
     if (kernel == ELBM_KERNEL_ROWS) return cudaErrorNotSupported;
-    ELBM_STORAGE_SWITCH(storage,
-                        (k_step<ST><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
-                            static_cast<const typename ST::S *>(fin), static_cast<typename ST::S *>(fout),
-                            g, p)));
+    if (g.ny <= 65535 && g.nz <= 65535) {
+        const dim3 grid(unsigned((g.nx + kStepBlock - 1) / kStepBlock), unsigned(g.ny), unsigned(g.nz));
+        ELBM_STORAGE_SWITCH(storage, (k_step<ST, true><<<grid, kStepBlock, 0, s>>>(
+                                         static_cast<const typename ST::S *>(fin),
+                                         static_cast<typename ST::S *>(fout), g, p)));
+    } else {
+        ELBM_STORAGE_SWITCH(storage, (k_step<ST, false><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
+                                         static_cast<const typename ST::S *>(fin),
+                                         static_cast<typename ST::S *>(fout), g, p)));
+    }
     return cudaGetLastError();
 }
 

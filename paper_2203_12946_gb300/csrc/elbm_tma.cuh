@@ -128,26 +128,27 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
     }
     __syncthreads();
 
-    uint64_t policy = 0;
-    if (threadIdx.x == 0) policy = l2_policy_evict_first();
+    const uint64_t policy = l2_policy_evict_first();
+    const int lane = threadIdx.x & 31;
 
-    // Issue the Q source rows of destination row `row` into stage `st` (thread 0).
+    // Issue the Q source rows of destination row `row` into stage `st`; called by
+    // warp 0 only: lane 0 posts the byte count, lane i < Q copies velocity i's row.
     auto issue = [&](int row, int st) {
+        if (lane == 0) mbar_arrive_expect_tx(&bar[st], uint32_t(Q) * row_bytes);
+        __syncwarp();
         const int y = row % g.ny, z = row / g.ny;
-        const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-        const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-        mbar_arrive_expect_tx(&bar[st], uint32_t(Q) * row_bytes);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
-            const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
-            const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+        for (int i = lane; i < Q; i += 32) {
+            const int cy = (D == 2 ? i : i / 3) % 3 - 1;  // velocity component along y
+            const int cz = D == 3 ? i % 3 - 1 : 0;        // along z (D3Q27)
+            int sy = y - cy, sz = z - cz;                  // pull: source row of velocity i
+            sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
+            sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
             const S *src = fin + (int64_t)i * g.N + ((int64_t)sz * g.ny + sy) * g.nx;
             bulk_copy_g2s(tiles + ((size_t)st * Q + i) * NXMAX, src, row_bytes, &bar[st], policy);
         }
     };
 
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
 #pragma unroll
         for (int s = 0; s < STAGES; ++s) {
             const int row = int(blockIdx.x) + s * G;
@@ -177,13 +178,13 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
                 f[i] = ST::load(tile[i * NXMAX + sx], T(weight(D, i)), rho0);
             }
             int br;
-            node_collide<D, T, true>(f, xd, p, &br);
+            collide<D, T, true>(f, xd, p, &br);
 #pragma unroll
             for (int i = 0; i < Q; ++i)
                 __stcs(fout + (int64_t)i * g.N + rowbase + x, ST::store(f[i], T(weight(D, i)), rho0));
         }
         __syncthreads(); // every read of this stage is done before it is refilled
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             const int next = row + STAGES * G;
             if (next < rows) issue(next, st);
         }
