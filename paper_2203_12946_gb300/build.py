@@ -55,6 +55,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    # extra preprocessor definitions for tuning experiments, e.g. "-DELBM_STEP_MIN_BLOCKS=6"
+    extra += os.environ.get("ELBM_NVCC_DEFINES", "").split()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

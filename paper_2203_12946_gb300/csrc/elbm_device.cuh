@@ -459,7 +459,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
     // x_i = (f^eq_i - f_i) / f_i with f^eq_i - f_i = w_i (drho + rho E_i) - d_i, and in
     // the same pass the x-only sums of Eq. alphaLowerCoeffs / qaud_tight_coeff and the
     // Omega- power sums (wasted only where the whole warp ends on the cutoff branch).
-    float2 xabs2 = f2(0.0f), xmin2 = f2(0.0f);
+    float xabs = 0.0f, xmin = 0.0f;
     float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f);
     float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
 #pragma unroll
@@ -469,8 +469,8 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         if (kPad && k == NP - 1) delta.y = 0.0f; // padding lane: f = 1, x = 0
         const float2 xi = pmul(delta, prcp(fp[k]));
         xp[k] = xi;
-        xabs2 = f2(fmaxf(xabs2.x, fabsf(xi.x)), fmaxf(xabs2.y, fabsf(xi.y)));
-        xmin2 = f2(fminf(xmin2.x, xi.x), fminf(xmin2.y, xi.y));
+        xabs = fmaxf(xabs, fmaxf(fabsf(xi.x), fabsf(xi.y))); // three-input max
+        xmin = fminf(xmin, fminf(xi.x, xi.y));
         const float2 fx2 = pmul(delta, xi); // f x^2
         const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
         const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
@@ -485,7 +485,6 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         S5 = pfma(q, xm2, S5);
         S6 = pfma(pmul(q, xm), xm2, S6);
     }
-    const float xabs = fmaxf(xabs2.x, xabs2.y), xmin = fminf(xmin2.x, xmin2.y);
 
     float alpha = 2.0f;
     int br = kBranchCutoff;

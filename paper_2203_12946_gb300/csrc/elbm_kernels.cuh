@@ -36,8 +36,19 @@ __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x
 // One node per thread.  Launched either on a 3D grid (x from blockIdx.x,
 // y = blockIdx.y, z = blockIdx.z: no index arithmetic) or, when ny or nz exceed
 // the grid limits, on a 1D grid over all nodes.
+// Minimum resident blocks per SM requested from the register allocator for the
+// direct step kernel (0: let the compiler choose).
+#ifndef ELBM_STEP_MIN_BLOCKS
+#define ELBM_STEP_MIN_BLOCKS 0
+#endif
+#if ELBM_STEP_MIN_BLOCKS > 0
+#define ELBM_STEP_BOUNDS __launch_bounds__(kStepBlock, ELBM_STEP_MIN_BLOCKS)
+#else
+#define ELBM_STEP_BOUNDS __launch_bounds__(kStepBlock)
+#endif
+
 template <class ST, bool kGrid3D>
-__global__ void __launch_bounds__(kStepBlock) k_step(const typename ST::S *__restrict__ fin,
+__global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
                                                     typename ST::S *__restrict__ fout, Geometry g,
                                                     CollideParams p)
 {

@@ -102,6 +102,14 @@ constexpr size_t rows_smem_bytes()
 // ---------------------------------------------------------------------------
 // The fused step over staged rows.  Requirements (checked by the launcher):
 // nx <= NXMAX, nx * sizeof(S) % 16 == 0, 16-byte aligned buffers.
+//
+// Stage hand-off without CTA barriers: every warp waits for the stage's
+// mbarrier, collides its nodes of the row, and then increments the stage's
+// release counter; the warp that brings the counter to the number of warps is
+// the last reader of that stage, so it resets the counter and issues the bulk
+// copies of the row STAGES iterations ahead into it.  A warp whose bounded wait
+// expires raises the CTA's abort flag (the other warps see it in their own
+// waits) and the error word; the CTA then lets its issued copies land and exits.
 // ---------------------------------------------------------------------------
 template <int D, class ST, int NXMAX, int NT, int STAGES>
 __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restrict__ fin,
@@ -111,36 +119,51 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
     using S = typename ST::S;
     using T = typename ST::T;
     constexpr int Q = Lattice<D>::Q;
+    constexpr int NW = NT / 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S *tiles = reinterpret_cast<S *>(smem_raw); // [STAGES][Q][NXMAX]
     __shared__ uint64_t bar[STAGES];
+    __shared__ int released[STAGES];
+    __shared__ int armed[STAGES]; // iteration index last issued into each stage
+    __shared__ volatile int abort_flag;
 
     const int rows = g.ny * g.nz;
     const int G = gridDim.x;
     if (int(blockIdx.x) >= rows) return; // uniform over the CTA
     const uint32_t row_bytes = uint32_t(g.nx) * uint32_t(sizeof(S));
     const T rho0 = T(p.rho0);
+    const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bar[s], 1);
+            released[s] = 0;
+            armed[s] = -1;
+        }
+        abort_flag = 0;
         mbar_fence_init();
     }
     __syncthreads();
 
     const uint64_t policy = l2_policy_evict_first();
-    const int lane = threadIdx.x & 31;
 
-    // Issue the Q source rows of destination row `row` into stage `st`; called by
-    // warp 0 only: lane 0 posts the byte count, lane i < Q copies velocity i's row.
-    auto issue = [&](int row, int st) {
-        if (lane == 0) mbar_arrive_expect_tx(&bar[st], uint32_t(Q) * row_bytes);
+    // Issue the Q source rows of iteration k (destination row blockIdx.x + k G) into
+    // stage k % STAGES; called by one whole warp: lane 0 posts the byte count, lane
+    // i < Q copies velocity i's source row.
+    auto issue = [&](int k) {
+        const int row = int(blockIdx.x) + k * G;
+        const int st = k % STAGES;
+        if (lane == 0) {
+            armed[st] = k;
+            mbar_arrive_expect_tx(&bar[st], uint32_t(Q) * row_bytes);
+        }
         __syncwarp();
         const int y = row % g.ny, z = row / g.ny;
         for (int i = lane; i < Q; i += 32) {
-            const int cy = (D == 2 ? i : i / 3) % 3 - 1;  // velocity component along y
-            const int cz = D == 3 ? i % 3 - 1 : 0;        // along z (D3Q27)
-            int sy = y - cy, sz = z - cz;                  // pull: source row of velocity i
+            const int cy = (D == 2 ? i : i / 3) % 3 - 1; // velocity component along y
+            const int cz = D == 3 ? i % 3 - 1 : 0;       // along z (D3Q27)
+            int sy = y - cy, sz = z - cz;                 // pull: source row of velocity i
             sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
             sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
             const S *src = fin + (int64_t)i * g.N + ((int64_t)sz * g.ny + sy) * g.nx;
@@ -148,21 +171,32 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
         }
     };
 
+    const int iters = (rows - int(blockIdx.x) + G - 1) / G;
     if (threadIdx.x < 32) {
-#pragma unroll
-        for (int s = 0; s < STAGES; ++s) {
-            const int row = int(blockIdx.x) + s * G;
-            if (row < rows) issue(row, s);
-        }
+        for (int k = 0; k < STAGES && k < iters; ++k) issue(k);
     }
+    __syncthreads(); // the first stages are armed before anyone waits on them
 
-    int k = 0;
     bool aborted = false;
-    for (int row = int(blockIdx.x); row < rows; row += G, ++k) {
+    for (int k = 0; k < iters; ++k) {
+        const int row = int(blockIdx.x) + k * G;
         const int st = k % STAGES;
         const uint32_t parity = uint32_t(k / STAGES) & 1u;
-        const bool ok = mbar_wait_bounded(&bar[st], parity);
-        if (__syncthreads_or(!ok)) {
+        // bounded wait, abandoned as soon as another warp has aborted
+        bool ok = mbar_try_wait(&bar[st], parity);
+        if (!ok) {
+            const unsigned long long t0 = global_ns();
+            while (!ok) {
+                for (int n = 0; n < 256 && !ok; ++n) ok = mbar_try_wait(&bar[st], parity);
+                if (ok) break;
+                if (abort_flag || global_ns() - t0 > kWaitLimitNs) break;
+            }
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                abort_flag = 1;
+                atomicExch(err, ELBM_ERR_TIMEOUT);
+            }
             aborted = true;
             break;
         }
@@ -183,22 +217,32 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
             for (int i = 0; i < Q; ++i)
                 __stcs(fout + (int64_t)i * g.N + rowbase + x, ST::store(f[i], T(weight(D, i)), rho0));
         }
-        __syncthreads(); // every read of this stage is done before it is refilled
-        if (threadIdx.x < 32) {
-            const int next = row + STAGES * G;
-            if (next < rows) issue(next, st);
+        // release the stage; the last warp out refills it
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&released[st], 1) == NW - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            if (lane == 0) {
+                released[st] = 0;
+                __threadfence_block();
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (k + STAGES < iters) issue(k + STAGES);
         }
     }
 
-    if (aborted) {
+    __syncthreads();
+    if (aborted || abort_flag) {
         if (threadIdx.x == 0) {
             atomicExch(err, ELBM_ERR_TIMEOUT);
             // let the copies already issued land before the CTA's shared memory goes away
-            for (int j = k; j < k + STAGES; ++j) {
-                const int row = int(blockIdx.x) + j * G;
-                if (row >= rows) break;
-                mbar_wait_bounded(&bar[j % STAGES], uint32_t(j / STAGES) & 1u);
-            }
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s] >= 0) mbar_wait_bounded(&bar[s], uint32_t(armed[s] / STAGES) & 1u);
         }
         __syncthreads();
     }
