@@ -386,6 +386,123 @@ def run_gpu(args):
     return 0
 
 
+def run_ensemble(args):
+    """Batched ensemble: 64 independent periodic D2Q9 domains, sides drawn from
+    {64, 96, 128, 192, 256, 384, 512}, beta ~ U[0.9, 0.999], random-phase vortex
+    initial velocity (spectrum peaked at k = 4, rms 0.03), FP32.  Times K steps as one
+    CUDA-graph replay of the batched launches and as one launch per domain and step."""
+    import torch
+
+    from paper_2203_12946_gb300 import elbm as E
+    from paper_2203_12946_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(inputs.DEFAULT_SEED)
+    sides = rng.choice([64, 96, 128, 192, 256, 384, 512], size=64)
+    betas = rng.uniform(0.9, 0.999, size=64)
+    dims = [(int(L_), int(L_), 1) for L_ in sides]
+    nodes = int(sum(L_ * L_ for L_ in sides))
+    res = {}
+    with E.Ensemble(E.ELBM_D2Q9, dims, list(betas), storage=args.storage) as ens:
+        for k, d in enumerate(dims):
+            rho, u = inputs.random_vortex_2d(d[0], rms=0.03, seed=k)
+            ens.init_equilibrium(k, rho, u)
+        bx, tune_ms = ens.tune()
+        for name, mode in (("graph", E.ELBM_BATCH_GRAPH), ("per_domain", E.ELBM_BATCH_PER_DOMAIN)):
+            ens.step(args.warmup, mode)
+            ens.synchronize()
+            t0 = time.perf_counter()
+            ens.step(args.steps, mode)
+            ens.synchronize()
+            dt = time.perf_counter() - t0
+            res[name] = nodes * args.steps / dt / 1e6
+        d = ens.diagnostics(0)
+    line = {
+        "metric": "aggregate MLUPS, 64-domain D2Q9 ensemble (sides 64..512), one CUDA-graph replay",
+        "value": res["graph"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched ensemble", "domains": 64, "nodes": nodes, "storage": args.storage,
+                   "block_width": bx, "tune_ms_per_step": tune_ms},
+        "per_domain_launches_mlups": res["per_domain"], "speedup_vs_per_domain": res["graph"] / res["per_domain"],
+        "domain0_alpha_range": [d["alpha_min"], d["alpha_max"]],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precision(args):
+    """Storage precision study on the doubly periodic shear layer (Sec. IV setup with
+    w = delta = 0.05, U0 = 0.04): D2Q9 1024^2, beta = 0.9995, FP64 / FP32 / FP16- and
+    BF16-deviation storage on the GPU; velocity and density errors against the FP64 run
+    at the checkpoints, MLUPS of each storage, and the FP64 run against the CPU oracle."""
+    import torch
+
+    from paper_2203_12946_gb300 import elbm as E
+    from paper_2203_12946_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    Ls = args.shear_L
+    dims = (Ls, Ls, 1)
+    beta = 0.9995
+    X, Y, _ = inputs.grid(dims)
+    rho0, u0 = inputs.shear_layer_2d(X, Y, Ls)
+    checkpoints = sorted(int(c) for c in args.checkpoints.split(","))
+    fields, rates = {}, {}
+    for storage in ("f64", "f32", "f16dev", "bf16dev"):
+        with E.Simulation(E.ELBM_D2Q9, dims, beta, storage=storage) as sim:
+            sim.init_equilibrium(rho0, u0)
+            done = 0
+            out = {}
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t_steps, t_ms = 0, 0.0
+            for c in checkpoints:
+                e0.record(stream)
+                sim.step(c - done)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_ms += e0.elapsed_time(e1)
+                t_steps += c - done
+                done = c
+                r, u = sim.moments()
+                out[c] = (r.cpu().numpy(), u.cpu().numpy())
+                d = sim.diagnostics(allow_nonphysical=True)
+                out[c] += (d["n_nonpositive"],)
+            fields[storage] = out
+            rates[storage] = Ls * Ls * t_steps / (t_ms / 1e3) / 1e6
+    table = {}
+    for storage in ("f32", "f16dev", "bf16dev"):
+        rows = {}
+        for c in checkpoints:
+            r64, u64, _ = fields["f64"][c]
+            r, u, bad = fields[storage][c]
+            rows[str(c)] = {
+                "u_rel_l2": float(np.linalg.norm(u - u64) / np.linalg.norm(u64)),
+                "u_linf_over_U0": float(np.max(np.abs(u - u64)) / 0.04),
+                "rho_linf": float(np.max(np.abs(r - r64))),
+                "nonpositive_nodes": int(bad),
+            }
+        table[storage] = rows
+    # the FP64 GPU run against the CPU oracle over the first steps
+    import oracle as O
+    ko = args.oracle_steps
+    fo, *_ = O.step(2, dims, O.init_equilibrium(2, rho0, u0), beta, nsteps=ko)
+    with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64") as sim:
+        sim.init_equilibrium(rho0, u0)
+        sim.step(ko)
+        fg = sim.get_populations()
+    line = {
+        "metric": "velocity error vs FP64 and MLUPS per storage, D2Q9 1024^2 shear layer",
+        "config": {"workload": "doubly periodic shear layer", "dims": [Ls, Ls], "beta": beta, "U0": 0.04,
+                   "w": 0.05, "delta": 0.05, "checkpoints": checkpoints,
+                   "l2": "both buffers fit in L2 at FP32 and below (L2-resident, not HBM-bound)"},
+        "errors_vs_fp64": table, "mlups": rates,
+        "fp64_vs_oracle": {"steps": ko, "max_rel_f": float(np.max(np.abs(fg - fo) / fo))},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,6 +513,12 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "direct", "rows"], default="auto")
+    ap.add_argument("--workload", choices=["tgv3d", "ensemble", "precision"], default="tgv3d",
+                    help="tgv3d: the benchmark (D3Q27 256^3); ensemble: batched D2Q9 domains; "
+                         "precision: storage error study on the D2Q9 shear layer")
+    ap.add_argument("--shear-L", type=int, default=1024)
+    ap.add_argument("--checkpoints", default="1000,5000,20000")
+    ap.add_argument("--oracle-steps", type=int, default=50)
     ap.add_argument("--storage", choices=["f32", "f16dev", "bf16dev"], default=STORAGE)
     ap.add_argument("--L", type=int, default=L, help="domain side (profiling runs only; "
                     "the benchmark workload is 256)")
@@ -406,6 +529,10 @@ def main():
         set_side(args.L)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_gpu(args)
 
 

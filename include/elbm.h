@@ -231,6 +231,55 @@ int elbm_step_count(const elbm_t *h, int64_t *steps);
 int elbm_synchronize(elbm_t *h);
 
 /* ---------------------------------------------------------------------------
+ * Batched ensembles.  The paper has no counterpart (a library service): many
+ * independent periodic domains of one lattice, each with its own dims and
+ * beta, held in one pair of device buffers and advanced together, so that
+ * domains too small to fill the GPU alone share every launch.
+ *
+ * Each domain's populations are one block in the layout described above
+ * (Q*N_d elements, SoA), so the per-domain calls below behave like their
+ * single-handle counterparts.  All calls enqueue on the batch's stream
+ * (opts->stream, or a stream the batch creates when that is NULL, since CUDA
+ * graphs cannot be captured on the legacy default stream); host transfers
+ * synchronise it.  Errors as for the single-domain calls; messages in
+ * elbm_batch_last_error.
+ * ------------------------------------------------------------------------- */
+typedef struct elbm_batch elbm_batch_t;
+
+/* How elbm_batch_step issues its n steps.  GRAPH: one launch per step over the
+ * work items of every domain, the n launches captured once (per n and buffer
+ * parity) into a CUDA graph that is replayed; LAUNCHES: the same launches
+ * issued one by one; PER_DOMAIN: one single-domain launch per domain and step
+ * (the baseline the batched forms are measured against). */
+#define ELBM_BATCH_GRAPH 0
+#define ELBM_BATCH_LAUNCHES 1
+#define ELBM_BATCH_PER_DOMAIN 2
+
+/* ndomains >= 1 domains; dims: 3 values per domain (each in [1, 65535], nz = 1
+ * for D2Q9); beta: one value per domain in (0, 1).  opts as for elbm_create
+ * (kernel is ignored).  Allocates both population buffers. */
+int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64_t *dims, const double *beta,
+                      const elbm_opts *opts);
+void elbm_batch_destroy(elbm_batch_t *b);
+const char *elbm_batch_last_error(const elbm_batch_t *b);
+/* Number of domains, total nodes and the current work-item width. */
+int elbm_batch_info(const elbm_batch_t *b, int *ndomains, int64_t *nodes, int *block_width);
+/* Per-domain initial state f = f^eq(rho, u) (rho may be NULL: rho0). */
+int elbm_batch_init_equilibrium(elbm_batch_t *b, int domain, const double *rho, const double *u, int where);
+/* Advances every domain by n >= 0 steps in the given mode (ELBM_BATCH_*). */
+int elbm_batch_step(elbm_batch_t *b, int64_t n, int mode);
+/* Times the candidate work-item widths (64, 128, 256 nodes) on the current
+ * state -- trial steps read the current buffer and write the other, so the
+ * state is unchanged -- and keeps the fastest.  chosen (may be NULL) receives
+ * it; ms_per_step (may be NULL) three timings in that order.  Synchronises. */
+int elbm_batch_tune(elbm_batch_t *b, int *chosen, double *ms_per_step);
+int elbm_batch_moments(elbm_batch_t *b, int domain, double *rho_out, double *u_out, int where);
+int elbm_batch_diagnostics(elbm_batch_t *b, int domain, elbm_diag *out, int64_t *alpha_hist);
+int elbm_batch_get_populations(elbm_batch_t *b, int domain, void *dst, int where);
+int elbm_batch_set_populations(elbm_batch_t *b, int domain, const void *src, int where);
+int elbm_batch_synchronize(elbm_batch_t *b);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free diagnostics.  The paper has no counterpart: this is a
  * service of the library for callers that cannot allocate device memory (an
  * application whose GPU memory belongs to another allocator or a fixed pool,

@@ -313,6 +313,36 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
 }
 
 // --------------------------------------------------------------------------
+// Batched ensemble: one launch advances every domain of the batch.  Work item
+// (domain, y, z, x0) covers nodes x0 .. x0 + BX - 1 of one x-row; the item
+// table is built on the host, so the kernel does no index division.  Each
+// domain has its own beta; everything else is the single-domain step.
+// --------------------------------------------------------------------------
+template <class ST, int BX>
+__global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restrict__ fin,
+                                                  typename ST::S *__restrict__ fout,
+                                                  const BatchDomain *__restrict__ doms,
+                                                  const int4 *__restrict__ items, CollideParams p)
+{
+    using T = typename ST::T;
+    const int4 it = __ldg(items + blockIdx.x);
+    const BatchDomain dm = doms[it.x];
+    const int x = it.w + int(threadIdx.x);
+    if (x >= dm.nx) return;
+    const Geometry g{dm.nx, dm.ny, dm.nz, dm.N};
+    p.beta = dm.beta;
+    const int64_t n = ((int64_t)it.z * dm.ny + it.y) * dm.nx + x;
+    T f[Q], xd[Q];
+    const T rho0 = T(p.rho0);
+    pull_load<D, ST>(fin + dm.off, g, x, it.y, it.z, rho0, f);
+    int br;
+    collide<D, T, true>(f, xd, p, &br);
+    typename ST::S *out = fout + dm.off;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) __stcs(out + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
+}
+
+// --------------------------------------------------------------------------
 // Launchers (storage dispatch).
 // --------------------------------------------------------------------------
 #define ELBM_STORAGE_SWITCH(storage, CALL)                                                     \
@@ -427,6 +457,26 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
                                          static_cast<const typename ST::S *>(fin),
                                          static_cast<typename ST::S *>(fout), g, p)));
     }
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_step_batch, ELBM_SUFFIX)(int storage, const void *fin, void *fout,
+                                                     const BatchDomain *doms, const int4 *items, int nitems,
+                                                     int bx, const CollideParams &p, cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (nitems <= 0) return cudaSuccess;
+#define ELBM_BATCH_BX(BXV)                                                                             \
+    ELBM_STORAGE_SWITCH(storage, (k_step_batch<ST, BXV><<<unsigned(nitems), BXV, 0, s>>>(               \
+                                     static_cast<const typename ST::S *>(fin),                          \
+                                     static_cast<typename ST::S *>(fout), doms, items, p)))
+    switch (bx) {
+    case 64: ELBM_BATCH_BX(64); break;
+    case 128: ELBM_BATCH_BX(128); break;
+    case 256: ELBM_BATCH_BX(256); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef ELBM_BATCH_BX
     return cudaGetLastError();
 }
 

@@ -13,6 +13,15 @@ namespace eelbm {
 struct Geometry;
 struct CollideParams;
 
+// One domain of a batched ensemble: its own periodic box, populations at
+// element offset `off` of the shared buffers (SoA [Q][N] inside), and beta.
+struct BatchDomain {
+    int nx, ny, nz, pad;
+    int64_t N;
+    int64_t off;
+    double beta;
+};
+
 // Device-side accumulator of the diagnostics reduction (library scratch).
 struct DiagAcc {
     double sum[6];                 // mass, momentum x/y/z, H, sum of alpha
@@ -54,7 +63,10 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
                                       cudaStream_t s);                                               \
     cudaError_t launch_diag_##SUFFIX(int storage, const void *f, const Geometry &g,                 \
                                      const CollideParams &p, DiagAcc *acc, int num_sms,             \
-                                     cudaStream_t s);
+                                     cudaStream_t s);                                                \
+    cudaError_t launch_step_batch_##SUFFIX(int storage, const void *fin, void *fout,                \
+                                           const BatchDomain *doms, const int4 *items, int nitems,   \
+                                           int bx, const CollideParams &p, cudaStream_t s);
 
 // Sets the message returned by elbm_last_error(NULL) (calls without a handle).
 void set_handle_free_error(const char *msg);

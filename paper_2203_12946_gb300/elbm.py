@@ -34,6 +34,7 @@ ELBM_ALPHA_HIGHER, ELBM_ALPHA_LOWER, ELBM_ALPHA_LBGK = 0, 1, 2
 ELBM_B_DERIVED, ELBM_B_PRINTED = 0, 1
 ELBM_MEM_DEVICE, ELBM_MEM_HOST = 0, 1
 ELBM_KERNEL_AUTO, ELBM_KERNEL_DIRECT, ELBM_KERNEL_ROWS = 0, 1, 2
+ELBM_BATCH_GRAPH, ELBM_BATCH_LAUNCHES, ELBM_BATCH_PER_DOMAIN = 0, 1, 2
 ELBM_BRANCH_CUTOFF, ELBM_BRANCH_SOLVED, ELBM_BRANCH_CLAMPED = 0, 1, 2
 ELBM_HIST_BINS = 256
 
@@ -45,7 +46,11 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
             "elbm_last_error", "elbm_bind_buffers", "elbm_set_stream", "elbm_init_equilibrium",
             "elbm_step", "elbm_moments", "elbm_alpha_field", "elbm_diagnostics",
             "elbm_get_populations", "elbm_set_populations", "elbm_step_count", "elbm_synchronize",
-            "elbm_diagnostics_noalloc"]
+            "elbm_diagnostics_noalloc",
+            "elbm_batch_create", "elbm_batch_destroy", "elbm_batch_last_error", "elbm_batch_info",
+            "elbm_batch_init_equilibrium", "elbm_batch_step", "elbm_batch_tune", "elbm_batch_moments",
+            "elbm_batch_diagnostics", "elbm_batch_get_populations", "elbm_batch_set_populations",
+            "elbm_batch_synchronize"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -117,6 +122,21 @@ def load(build_if_missing: bool = True):
             "elbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(i64), ctypes.c_double,
                                                         ctypes.POINTER(elbm_opts), P,
                                                         ctypes.POINTER(elbm_diag), P]),
+            "elbm_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(elbm_opts)]),
+            "elbm_batch_destroy": (None, [P]),
+            "elbm_batch_last_error": (ctypes.c_char_p, [P]),
+            "elbm_batch_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
+                                               ctypes.POINTER(ctypes.c_int)]),
+            "elbm_batch_init_equilibrium": (ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
+            "elbm_batch_step": (ctypes.c_int, [P, i64, ctypes.c_int]),
+            "elbm_batch_tune": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+            "elbm_batch_moments": (ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
+            "elbm_batch_diagnostics": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(elbm_diag), P]),
+            "elbm_batch_get_populations": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
+            "elbm_batch_set_populations": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
+            "elbm_batch_synchronize": (ctypes.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -376,3 +396,162 @@ class Simulation:
     @property
     def steps(self):
         return elbm_step_count(self.h)
+
+
+# ----------------------------------------------------------------------------
+# Batched ensembles (same names as include/elbm.h)
+# ----------------------------------------------------------------------------
+
+def _bcheck(b, code, what):
+    if code != ELBM_OK:
+        msg = load().elbm_batch_last_error(b)
+        raise ElbmError(code, f"{what}: {msg.decode() if msg else ''}")
+
+
+def elbm_batch_create(lattice, dims_list, betas, opts: elbm_opts | None = None) -> int:
+    nd = len(dims_list)
+    flat = []
+    for d in dims_list:
+        flat += [int(v) for v in (list(d) + [1, 1])[:3]]
+    b = ctypes.c_void_p(None)
+    _bcheck(None, load().elbm_batch_create(ctypes.byref(b), int(lattice), nd, (ctypes.c_int64 * (3 * nd))(*flat),
+                                           (ctypes.c_double * nd)(*[float(x) for x in betas]),
+                                           None if opts is None else ctypes.byref(opts)), "elbm_batch_create")
+    return b.value
+
+
+def elbm_batch_destroy(b) -> None:
+    load().elbm_batch_destroy(b)
+
+
+def elbm_batch_last_error(b=None) -> str:
+    m = load().elbm_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def elbm_batch_info(b):
+    nd, nodes, bx = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_int(0)
+    _bcheck(b, load().elbm_batch_info(b, ctypes.byref(nd), ctypes.byref(nodes), ctypes.byref(bx)),
+            "elbm_batch_info")
+    return nd.value, nodes.value, bx.value
+
+
+def elbm_batch_init_equilibrium(b, domain, rho, u, where=ELBM_MEM_HOST) -> None:
+    _bcheck(b, load().elbm_batch_init_equilibrium(b, int(domain), _ptr(rho), _ptr(u), int(where)),
+            "elbm_batch_init_equilibrium")
+
+
+def elbm_batch_step(b, n=1, mode=ELBM_BATCH_GRAPH) -> None:
+    _bcheck(b, load().elbm_batch_step(b, int(n), int(mode)), "elbm_batch_step")
+
+
+def elbm_batch_tune(b):
+    chosen = ctypes.c_int(0)
+    ms = (ctypes.c_double * 3)()
+    _bcheck(b, load().elbm_batch_tune(b, ctypes.byref(chosen), ms), "elbm_batch_tune")
+    return chosen.value, list(ms)
+
+
+def elbm_batch_moments(b, domain, rho_out, u_out, where=ELBM_MEM_HOST) -> None:
+    _bcheck(b, load().elbm_batch_moments(b, int(domain), _ptr(rho_out), _ptr(u_out), int(where)),
+            "elbm_batch_moments")
+
+
+def elbm_batch_diagnostics(b, domain, alpha_hist=None) -> dict:
+    d = elbm_diag()
+    _bcheck(b, load().elbm_batch_diagnostics(b, int(domain), ctypes.byref(d), _ptr(alpha_hist)),
+            "elbm_batch_diagnostics")
+    return d.as_dict()
+
+
+def elbm_batch_get_populations(b, domain, dst, where=ELBM_MEM_HOST) -> None:
+    _bcheck(b, load().elbm_batch_get_populations(b, int(domain), _ptr(dst), int(where)),
+            "elbm_batch_get_populations")
+
+
+def elbm_batch_set_populations(b, domain, src, where=ELBM_MEM_HOST) -> None:
+    _bcheck(b, load().elbm_batch_set_populations(b, int(domain), _ptr(src), int(where)),
+            "elbm_batch_set_populations")
+
+
+def elbm_batch_synchronize(b) -> None:
+    _bcheck(b, load().elbm_batch_synchronize(b), "elbm_batch_synchronize")
+
+
+class Ensemble:
+    """Independent periodic domains advanced together (see the batched-ensemble
+    section of include/elbm.h)."""
+
+    _DT = {ELBM_STORE_F64: np.float64, ELBM_STORE_F32: np.float32, ELBM_STORE_F16DEV: np.float16,
+           ELBM_STORE_BF16DEV: np.uint16}
+
+    def __init__(self, lattice, dims_list, betas, storage="f32", alpha_mode=ELBM_ALPHA_HIGHER, cutoff=True,
+                 b_variant=ELBM_B_DERIVED, device=0, rho0=1.0, stream=None):
+        self.lattice = int(lattice)
+        self.D = 2 if self.lattice == ELBM_D2Q9 else 3
+        self.Q = self.lattice
+        self.dims = [tuple(int(v) for v in (list(d) + [1, 1])[:3]) for d in dims_list]
+        self.storage = STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+        o = elbm_default_opts()
+        o.storage = self.storage
+        o.alpha_mode = int(alpha_mode)
+        o.cutoff = int(bool(cutoff))
+        o.b_variant = int(b_variant)
+        o.device = int(device)
+        o.rho0 = float(rho0)
+        o.stream = None if stream is None else int(stream)
+        self.b = elbm_batch_create(self.lattice, self.dims, betas, o)
+
+    def close(self):
+        if getattr(self, "b", None):
+            elbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def nodes(self, d):
+        nx, ny, nz = self.dims[d]
+        return nx * ny * nz
+
+    def init_equilibrium(self, d, rho, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+        elbm_batch_init_equilibrium(self.b, d, rho, u, ELBM_MEM_HOST)
+
+    def step(self, n=1, mode=ELBM_BATCH_GRAPH):
+        elbm_batch_step(self.b, n, mode)
+
+    def tune(self):
+        return elbm_batch_tune(self.b)
+
+    def moments(self, d):
+        N = self.nodes(d)
+        rho = np.empty(N)
+        u = np.empty((self.D, N))
+        elbm_batch_moments(self.b, d, rho, u, ELBM_MEM_HOST)
+        return rho, u
+
+    def diagnostics(self, d):
+        return elbm_batch_diagnostics(self.b, d)
+
+    def get_populations(self, d):
+        out = np.empty((self.Q, self.nodes(d)), dtype=self._DT[self.storage])
+        elbm_batch_get_populations(self.b, d, out, ELBM_MEM_HOST)
+        return out
+
+    def set_populations(self, d, f):
+        f = np.ascontiguousarray(f, dtype=self._DT[self.storage]).reshape(self.Q, self.nodes(d))
+        elbm_batch_set_populations(self.b, d, f, ELBM_MEM_HOST)
+
+    def synchronize(self):
+        elbm_batch_synchronize(self.b)

@@ -129,3 +129,18 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     with pytest.raises(ImportError):
         E.load(build_if_missing=False)
     monkeypatch.setattr(E, "_lib", None)
+
+
+@pytest.mark.parametrize("lattice,dims,betas,code", [
+    (8, [(8, 8, 1)], [0.9], E.ELBM_ERR_ARG),
+    (E.ELBM_D2Q9, [], [], E.ELBM_ERR_ARG),
+    (E.ELBM_D2Q9, [(8, 8, 2)], [0.9], E.ELBM_ERR_ARG),
+    (E.ELBM_D2Q9, [(8, 8, 1), (0, 8, 1)], [0.9, 0.9], E.ELBM_ERR_ARG),
+    (E.ELBM_D3Q27, [(8, 8, 8), (70000, 2, 2)], [0.9, 0.9], E.ELBM_ERR_ARG),
+    (E.ELBM_D3Q27, [(8, 8, 8), (4, 4, 4)], [0.9, 1.0], E.ELBM_ERR_ARG),
+])
+def test_batch_create_rejects_bad_arguments(lib, lattice, dims, betas, code):
+    with pytest.raises(E.ElbmError) as ei:
+        E.elbm_batch_create(lattice, dims, betas)
+    assert ei.value.code == code
+    assert "elbm_batch_create" in E.elbm_batch_last_error(None)
