@@ -111,6 +111,12 @@ def _load():
             "or_moments_field": (None, [ctypes.c_int, _i64, _D, _D, _D]),
             "or_H_total": (ctypes.c_double, [ctypes.c_int, _i64, _D]),
             "or_max_threads": (ctypes.c_int, []),
+            "or_collide_vjp": (None, [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_double, _D]),
+            "or_step_adjoint": (None, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                       ctypes.c_int]),
+            "or_kinetic_energy": (ctypes.c_double, [ctypes.c_int, _i64, _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -327,3 +333,36 @@ def step(D: int, dims, f, beta: float, cutoff: bool = True, b_variant: int = B_D
                     _dp(dh), int(nthreads))
         a, b = b, a
     return a, alpha_, br, dh
+
+
+# ----------------------------------------------------------------------------
+# Adjoint (chain rule through the step; node Jacobians by central differences)
+# ----------------------------------------------------------------------------
+
+def collide_vjp(D: int, f, g, beta: float, cutoff: bool = False, b_variant: int = B_DERIVED,
+                mode: int = MODE_HIGHER, eps: float = 1e-5) -> np.ndarray:
+    """h = J^T g of one node's collision (J = d f* / d f), by central differences."""
+    f, g = _f64(f), _f64(g)
+    h = np.zeros_like(f)
+    _load().or_collide_vjp(D, _dp(f), _dp(g), float(beta), int(bool(cutoff)), int(b_variant), int(mode),
+                           float(eps), _dp(h))
+    return h
+
+
+def step_adjoint(D: int, dims, f_t, g_next, beta: float, cutoff: bool = False, b_variant: int = B_DERIVED,
+                 mode: int = MODE_HIGHER, eps: float = 1e-5, nthreads: int = 0) -> np.ndarray:
+    """dL/df^t from dL/df^{t+1} for f^{t+1} = collide(stream(f^t))."""
+    nx, ny, nz = _dims(D, dims)
+    f_t, g_next = _f64(f_t), _f64(g_next)
+    g_t = np.zeros_like(f_t)
+    _load().or_step_adjoint(D, nx, ny, nz, float(beta), int(bool(cutoff)), int(b_variant), int(mode),
+                            _dp(f_t), _dp(g_next), _dp(g_t), float(eps), int(nthreads))
+    return g_t
+
+
+def kinetic_energy(D: int, f, want_grad: bool = True):
+    """(L, dL/df) with L = 1/2 sum rho |u|^2."""
+    f = _f64(f)
+    g = np.zeros_like(f) if want_grad else None
+    L = _load().or_kinetic_energy(D, f.shape[1], _dp(f), _dp(g))
+    return float(L), g

@@ -564,3 +564,109 @@ int or_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint (reverse-mode derivative) of the step, for checking a hand-written */
+/* backward pass.  The paper defines no adjoint; this is the chain rule       */
+/* applied to the step above, with each node's Jacobian-transpose product     */
+/* taken by central differences of the node collision in FP64 (relative step  */
+/* eps on each population).  Streaming is a permutation, so its adjoint is    */
+/* the inverse permutation: pull by c_i becomes push by c_i.                  */
+/* ------------------------------------------------------------------------ */
+
+/* One node: f (pre-collision, Q values) -> f* (Eq. fstar_def with alpha). */
+static void or_collide_node(int D, const double *f, double beta, int cutoff, int b_variant, int mode,
+                            double *fs)
+{
+    double feq[OR_QMAX], rho, u[3];
+    or_alpha_info info;
+    int Q = 1, a;
+    for (a = 0; a < D; a++) Q *= 3;
+    or_moments(D, f, &rho, u);
+    or_equilibrium(D, rho, u, feq);
+    or_alpha(Q, f, feq, beta, cutoff, b_variant, mode, &info);
+    or_relax(Q, f, feq, info.alpha, beta, fs);
+}
+
+/* h_j = sum_i g_i d f*_i / d f_j at one node, by central differences. */
+void or_collide_vjp(int D, const double *f, const double *g, double beta, int cutoff, int b_variant, int mode,
+                    double eps, double *h)
+{
+    double fp[OR_QMAX], fm[OR_QMAX], sp[OR_QMAX], sm[OR_QMAX];
+    int Q = 1, a, i, j;
+    for (a = 0; a < D; a++) Q *= 3;
+    for (j = 0; j < Q; j++) {
+        double d = eps * f[j], acc = 0.0;
+        memcpy(fp, f, sizeof(double) * Q);
+        memcpy(fm, f, sizeof(double) * Q);
+        fp[j] += d;
+        fm[j] -= d;
+        or_collide_node(D, fp, beta, cutoff, b_variant, mode, sp);
+        or_collide_node(D, fm, beta, cutoff, b_variant, mode, sm);
+        for (i = 0; i < Q; i++) acc += g[i] * (sp[i] - sm[i]);
+        h[j] = acc / (2.0 * d);
+    }
+}
+
+/* dL/df^t from dL/df^{t+1}, where f^{t+1} = collide(stream(f^t)) (fields SoA). */
+void or_step_adjoint(int D, int64_t nx, int64_t ny, int64_t nz, double beta, int cutoff, int b_variant, int mode,
+                     const double *f_t, const double *g_next, double *g_t, double eps, int nthreads)
+{
+    int c[OR_QMAX * 3];
+    double w[OR_QMAX];
+    int Q = or_lattice(D, c, w);
+    int64_t N = nx * ny * nz, z;
+    double *F = (double *)malloc(sizeof(double) * (size_t)Q * (size_t)N);
+    if (!F) return;
+    or_stream(D, nx, ny, nz, f_t, F, nthreads);
+    or_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; z++) {
+        int64_t y, xx;
+        for (y = 0; y < ny; y++)
+            for (xx = 0; xx < nx; xx++) {
+                int64_t n = (z * ny + y) * nx + xx;
+                double fn[OR_QMAX], gn[OR_QMAX], h[OR_QMAX];
+                int i;
+                for (i = 0; i < Q; i++) {
+                    fn[i] = F[(int64_t)i * N + n];
+                    gn[i] = g_next[(int64_t)i * N + n];
+                }
+                or_collide_vjp(D, fn, gn, beta, cutoff, b_variant, mode, eps, h);
+                /* F_i(x) = f^t_i(x - c_i): the adjoint sends h_i(x) back to x - c_i */
+                for (i = 0; i < Q; i++) {
+                    int64_t sx = or_wrap(xx - c[i * D + 0], nx);
+                    int64_t sy = or_wrap(y - c[i * D + 1], ny);
+                    int64_t sz = (D == 3) ? or_wrap(z - c[i * D + 2], nz) : 0;
+                    g_t[(int64_t)i * N + (sz * ny + sy) * nx + sx] = h[i];
+                }
+            }
+    }
+    free(F);
+}
+
+/* Kinetic energy L = 1/2 sum_x rho |u|^2 of a field and its gradient          */
+/* dL/df_i = c_i . u - |u|^2 / 2 at every node.                               */
+double or_kinetic_energy(int D, int64_t N, const double *f, double *grad)
+{
+    int c[OR_QMAX * 3];
+    double w[OR_QMAX];
+    int Q = or_lattice(D, c, w);
+    int64_t n;
+    double L = 0.0;
+    for (n = 0; n < N; n++) {
+        double fn[OR_QMAX], rho, u[3], uu = 0.0;
+        int i, a;
+        for (i = 0; i < Q; i++) fn[i] = f[(int64_t)i * N + n];
+        or_moments(D, fn, &rho, u);
+        for (a = 0; a < D; a++) uu += u[a] * u[a];
+        L += 0.5 * rho * uu;
+        if (grad)
+            for (i = 0; i < Q; i++) {
+                double cu = 0.0;
+                for (a = 0; a < D; a++) cu += c[i * D + a] * u[a];
+                grad[(int64_t)i * N + n] = cu - 0.5 * uu;
+            }
+    }
+    return L;
+}
