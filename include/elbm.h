@@ -222,6 +222,33 @@ int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist);
 int elbm_get_populations(elbm_t *h, void *dst, int where);
 int elbm_set_populations(elbm_t *h, const void *src, int where);
 
+/* ---------------------------------------------------------------------------
+ * Reverse-mode derivatives.  The paper has no adjoint; these are the chain
+ * rule through the step, for gradient-based studies (sensitivities of a loss
+ * with respect to the initial state).  Gradient arrays are SoA [Q][N] in the
+ * compute type of the handle (double for ELBM_STORE_F64, float otherwise),
+ * device memory, caller-owned.  All calls enqueue on the handle's stream.
+ * ------------------------------------------------------------------------- */
+
+/* One backward step.  f_t: the state BEFORE the step (storage type, Q*N,
+ * device); g_next = dL/df^{t+1}; writes g_t = dL/df^t, where
+ * f^{t+1} = collide(stream(f^t)).  The collision is differentiated through the
+ * equilibrium, x, the sign-split sums, alpha_Lower, h, alpha_Higher and the
+ * positivity clamp (the cutoff and clamp branches on the side the forward
+ * pass takes; Omega+/- membership held fixed).  g_t must not alias g_next. */
+int elbm_adjoint_step(elbm_t *h, const void *f_t, const void *g_next, void *g_t);
+
+/* L = 1/2 sum_x rho |u|^2 of the field f (storage type, device; NULL = the
+ * current state), accumulated in FP64 into *L (host; synchronises), and, if
+ * grad is not NULL, dL/df_i = c_i . u - |u|^2/2 (compute type, device). */
+int elbm_kinetic_energy(elbm_t *h, const void *f, double *L, void *grad);
+
+/* Derivatives of the initial state f = f^eq(rho, u) (elbm_init_equilibrium)
+ * with respect to rho and u, given g = dL/df (compute type): drho (N doubles,
+ * may be NULL) and du (D*N doubles, may be NULL); rho may be NULL (rho0).
+ * All arrays in device memory. */
+int elbm_equilibrium_vjp(elbm_t *h, const double *rho, const double *u, const void *g, double *drho, double *du);
+
 /* Steps taken since the last init/set. */
 int elbm_step_count(const elbm_t *h, int64_t *steps);
 

@@ -528,6 +528,47 @@ int elbm_set_populations(elbm_t *h, const void *src, int where)
     return ELBM_OK;
 }
 
+int elbm_adjoint_step(elbm_t *h, const void *f_t, const void *g_next, void *g_t)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_adjoint_step: handle is NULL");
+    if (!f_t || !g_next || !g_t) return fail(h, ELBM_ERR_ARG, "elbm_adjoint_step: null pointer");
+    if (g_next == g_t) return fail(h, ELBM_ERR_ARG, "elbm_adjoint_step: g_t must not alias g_next");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_step_adjoint, h->opts.storage, f_t, g_next, g_t, h->g, params_of(h),
+                                    h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_adjoint_step: kernel launch");
+    return ELBM_OK;
+}
+
+int elbm_kinetic_energy(elbm_t *h, const void *f, double *L, void *grad)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_kinetic_energy: handle is NULL");
+    if (!L) return fail(h, ELBM_ERR_ARG, "elbm_kinetic_energy: L is NULL");
+    if (!f && !h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_kinetic_energy: no state");
+    DeviceGuard guard(h->opts.device);
+    const void *src = f ? f : h->pop[h->cur];
+    double *acc = &h->acc->sum[0];
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double), h->stream);
+    if (e == cudaSuccess)
+        e = ELBM_BY_LATTICE(h, launch_kinetic_energy, h->opts.storage, src, h->g, h->opts.rho0, acc, grad, h->num_sms,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L, acc, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_kinetic_energy");
+    return ELBM_OK;
+}
+
+int elbm_equilibrium_vjp(elbm_t *h, const double *rho, const double *u, const void *g, double *drho, double *du)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_equilibrium_vjp: handle is NULL");
+    if (!u || !g) return fail(h, ELBM_ERR_ARG, "elbm_equilibrium_vjp: u or g is NULL");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_equilibrium_vjp, h->opts.storage, rho, u, g, h->g, h->opts.rho0, drho,
+                                    du, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_equilibrium_vjp: kernel launch");
+    return ELBM_OK;
+}
+
 int elbm_step_count(const elbm_t *h, int64_t *steps)
 {
     if (!h || !steps) return fail(nullptr, ELBM_ERR_ARG, "elbm_step_count: null argument");

@@ -16,6 +16,7 @@
 #include "elbm_device.cuh"
 #include "elbm_launch.h"
 #include "elbm_tma.cuh"
+#include "elbm_adjoint.cuh"
 
 namespace eelbm {
 namespace ELBM_SUFFIX {
@@ -343,6 +344,124 @@ __global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restr
 }
 
 // --------------------------------------------------------------------------
+// Adjoint of one step (f^{t+1} = collide(stream(f^t))): given gnext = dL/df^{t+1},
+// write gout = dL/df^t.  Per node x: the pre-collision populations F(x) are
+// pulled from f^t as in the step, h = J^T gnext(x) is the collision's VJP, and
+// the transpose of pull streaming sends h_i(x) to node x - c_i (a push).
+// Gradient arrays are SoA [Q][N] in the compute type.
+// --------------------------------------------------------------------------
+template <class ST>
+__global__ void __launch_bounds__(kAuxBlock) k_step_adjoint(const typename ST::S *__restrict__ fin,
+                                                           const typename ST::T *__restrict__ gnext,
+                                                           typename ST::T *__restrict__ gout, Geometry g,
+                                                           CollideParams p)
+{
+    using T = typename ST::T;
+    const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+    if (n >= g.N) return;
+    int x, y, z;
+    node_coords(n, g, x, y, z);
+    T F[Q], gl[Q], h[Q];
+    pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), F);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) gl[i] = gnext[(int64_t)i * g.N + n];
+    node_vjp<D, T>(F, gl, p, h);
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+        const int dx = cx == 1 ? xm : (cx == -1 ? xp : x);
+        const int dy = cy == 1 ? ym : (cy == -1 ? yp : y);
+        const int dz = cz == 1 ? zm : (cz == -1 ? zp : z);
+        gout[(int64_t)i * g.N + ((int64_t)dz * g.ny + dy) * g.nx + dx] = h[i];
+    }
+}
+
+// Kinetic energy L = 1/2 sum rho |u|^2 of a stored field (FP64 sum into acc[0])
+// and, optionally, its gradient dL/df_i = c_i . u - |u|^2 / 2.
+template <class ST>
+__global__ void __launch_bounds__(kAuxBlock) k_kinetic_energy(const typename ST::S *__restrict__ f,
+                                                             Geometry g, double rho0, double *__restrict__ acc,
+                                                             typename ST::T *__restrict__ grad)
+{
+    using T = typename ST::T;
+    double e = 0.0;
+    for (int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; n < g.N; n += (int64_t)gridDim.x * kAuxBlock) {
+        double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+        double fv[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            fv[i] = ST::load64(f[(int64_t)i * g.N + n], weight(D, i), rho0);
+            r += fv[i];
+#pragma unroll
+            for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * fv[i];
+        }
+        double uu = 0.0, u[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            u[a] = j[a] / r;
+            uu += u[a] * u[a];
+        }
+        e += 0.5 * r * uu;
+        if (grad) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                double cu = 0.0;
+#pragma unroll
+                for (int a = 0; a < D; ++a) cu += vel(D, i, a) * u[a];
+                grad[(int64_t)i * g.N + n] = T(cu - 0.5 * uu);
+            }
+        }
+    }
+    e = warp_sum(e);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, e);
+}
+
+// Derivatives of f = f^eq(rho, u) (the initial state) with respect to rho and u:
+// drho = sum_i g_i feq_i / rho, du_a = sum_i g_i feq_i d log phi_a(c_ia) / du_a.
+template <class T>
+__global__ void __launch_bounds__(kAuxBlock) k_equilibrium_vjp(const double *__restrict__ rho,
+                                                              const double *__restrict__ u,
+                                                              const T *__restrict__ gf, Geometry g, double rho_uniform,
+                                                              double *__restrict__ drho, double *__restrict__ du)
+{
+    const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+    if (n >= g.N) return;
+    const double r = rho ? rho[n] : rho_uniform;
+    double phi[3][3], dlp[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double ua = u[(int64_t)a * g.N + n];
+        const double s = sqrt(1.0 + 3.0 * ua * ua), Y = 2.0 - s, num = 2.0 * ua + s, den = 1.0 - ua;
+        const double zz = num / den, dY = -3.0 * ua / s, dlz = (2.0 + 3.0 * ua / s) / num + 1.0 / den;
+        phi[a][0] = Y / (6.0 * zz);
+        phi[a][1] = Y * (4.0 / 6.0);
+        phi[a][2] = Y * zz / 6.0;
+        dlp[a][0] = dY / Y - dlz;
+        dlp[a][1] = dY / Y;
+        dlp[a][2] = dY / Y + dlz;
+    }
+    double sr = 0.0, su[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        double v = r;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v *= phi[a][vel(D, i, a) + 1];
+        const double gv = double(gf[(int64_t)i * g.N + n]) * v;
+        sr += gv;
+#pragma unroll
+        for (int a = 0; a < D; ++a) su[a] += gv * dlp[a][vel(D, i, a) + 1];
+    }
+    if (drho) drho[n] = sr / r;
+    if (du) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) du[(int64_t)a * g.N + n] = su[a];
+    }
+}
+
+// --------------------------------------------------------------------------
 // Launchers (storage dispatch).
 // --------------------------------------------------------------------------
 #define ELBM_STORAGE_SWITCH(storage, CALL)                                                     \
@@ -477,6 +596,48 @@ cudaError_t ELBM_CAT(launch_step_batch, ELBM_SUFFIX)(int storage, const void *fi
     default: return cudaErrorInvalidValue;
     }
 #undef ELBM_BATCH_BX
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_step_adjoint, ELBM_SUFFIX)(int storage, const void *fin, const void *gnext,
+                                                       void *gout, const Geometry &g, const CollideParams &p,
+                                                       cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    ELBM_STORAGE_SWITCH(storage, (k_step_adjoint<ST><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
+                                     static_cast<const typename ST::S *>(fin),
+                                     static_cast<const typename ST::T *>(gnext), static_cast<typename ST::T *>(gout),
+                                     g, p)));
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_kinetic_energy, ELBM_SUFFIX)(int storage, const void *f, const Geometry &g, double rho0,
+                                                         double *acc, void *grad, int num_sms, cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    unsigned blocks = blocks_for(g.N, kAuxBlock);
+    const unsigned cap = unsigned(num_sms > 0 ? num_sms : 1) * 8u;
+    if (blocks > cap) blocks = cap;
+    ELBM_STORAGE_SWITCH(storage, (k_kinetic_energy<ST><<<blocks, kAuxBlock, 0, s>>>(
+                                     static_cast<const typename ST::S *>(f), g, rho0, acc,
+                                     static_cast<typename ST::T *>(grad))));
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_equilibrium_vjp, ELBM_SUFFIX)(int storage, const double *rho, const double *u,
+                                                          const void *gf, const Geometry &g, double rho_uniform,
+                                                          double *drho, double *du, cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    if (storage == ELBM_STORE_F64)
+        k_equilibrium_vjp<double><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
+            rho, u, static_cast<const double *>(gf), g, rho_uniform, drho, du);
+    else
+        k_equilibrium_vjp<float><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
+            rho, u, static_cast<const float *>(gf), g, rho_uniform, drho, du);
     return cudaGetLastError();
 }
 

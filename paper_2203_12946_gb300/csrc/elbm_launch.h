@@ -66,7 +66,17 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
                                      cudaStream_t s);                                                \
     cudaError_t launch_step_batch_##SUFFIX(int storage, const void *fin, void *fout,                \
                                            const BatchDomain *doms, const int4 *items, int nitems,   \
-                                           int bx, const CollideParams &p, cudaStream_t s);
+                                           int bx, const CollideParams &p, cudaStream_t s);          \
+    cudaError_t launch_step_adjoint_##SUFFIX(int storage, const void *fin, const void *gnext,       \
+                                             void *gout, const Geometry &g, const CollideParams &p,  \
+                                             cudaStream_t s);                                        \
+    cudaError_t launch_kinetic_energy_##SUFFIX(int storage, const void *f, const Geometry &g,       \
+                                               double rho0, double *acc, void *grad, int num_sms,    \
+                                               cudaStream_t s);                                      \
+    cudaError_t launch_equilibrium_vjp_##SUFFIX(int storage, const double *rho, const double *u,    \
+                                                const void *gf, const Geometry &g,                   \
+                                                double rho_uniform, double *drho, double *du,        \
+                                                cudaStream_t s);
 
 // Sets the message returned by elbm_last_error(NULL) (calls without a handle).
 void set_handle_free_error(const char *msg);

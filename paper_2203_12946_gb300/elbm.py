@@ -50,7 +50,7 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
             "elbm_batch_create", "elbm_batch_destroy", "elbm_batch_last_error", "elbm_batch_info",
             "elbm_batch_init_equilibrium", "elbm_batch_step", "elbm_batch_tune", "elbm_batch_moments",
             "elbm_batch_diagnostics", "elbm_batch_get_populations", "elbm_batch_set_populations",
-            "elbm_batch_synchronize"]
+            "elbm_batch_synchronize", "elbm_adjoint_step", "elbm_kinetic_energy", "elbm_equilibrium_vjp"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -137,6 +137,9 @@ def load(build_if_missing: bool = True):
             "elbm_batch_get_populations": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
             "elbm_batch_set_populations": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
             "elbm_batch_synchronize": (ctypes.c_int, [P]),
+            "elbm_adjoint_step": (ctypes.c_int, [P, P, P, P]),
+            "elbm_kinetic_energy": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_double), P]),
+            "elbm_equilibrium_vjp": (ctypes.c_int, [P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -258,6 +261,21 @@ def elbm_diagnostics_noalloc(lattice, dims, beta, populations, opts: elbm_opts |
     out = d.as_dict()
     out["status"] = code
     return out
+
+
+def elbm_adjoint_step(h, f_t, g_next, g_t) -> None:
+    _check(h, load().elbm_adjoint_step(h, _ptr(f_t), _ptr(g_next), _ptr(g_t)), "elbm_adjoint_step")
+
+
+def elbm_kinetic_energy(h, f=None, grad=None) -> float:
+    L = ctypes.c_double(0.0)
+    _check(h, load().elbm_kinetic_energy(h, _ptr(f), ctypes.byref(L), _ptr(grad)), "elbm_kinetic_energy")
+    return float(L.value)
+
+
+def elbm_equilibrium_vjp(h, rho, u, g, drho=None, du=None) -> None:
+    _check(h, load().elbm_equilibrium_vjp(h, _ptr(rho), _ptr(u), _ptr(g), _ptr(drho), _ptr(du)),
+           "elbm_equilibrium_vjp")
 
 
 def elbm_get_populations(h, dst, where=ELBM_MEM_DEVICE) -> None:
@@ -396,6 +414,37 @@ class Simulation:
     @property
     def steps(self):
         return elbm_step_count(self.h)
+
+    # -- device copies of the state and reverse-mode helpers ----------------
+    @property
+    def grad_dtype(self):
+        return self.torch.float64 if self.storage == ELBM_STORE_F64 else self.torch.float32
+
+    def state_copy(self):
+        """Device copy of the current populations (raw storage bytes)."""
+        buf = self.torch.empty(self.pop_bytes, dtype=self.torch.uint8, device=self.device)
+        elbm_get_populations(self.h, buf, ELBM_MEM_DEVICE)
+        return buf
+
+    def restore(self, buf):
+        elbm_set_populations(self.h, buf, ELBM_MEM_DEVICE)
+
+    def adjoint_step(self, f_t, g_next):
+        g_t = self.torch.empty_like(g_next)
+        elbm_adjoint_step(self.h, f_t, g_next, g_t)
+        return g_t
+
+    def kinetic_energy(self, f=None, with_grad=False):
+        grad = (self.torch.empty((self.Q, self.N), dtype=self.grad_dtype, device=self.device)
+                if with_grad else None)
+        L = elbm_kinetic_energy(self.h, f, grad)
+        return (L, grad) if with_grad else L
+
+    def equilibrium_vjp(self, rho, u, g):
+        drho = self.torch.empty(self.N, dtype=self.torch.float64, device=self.device)
+        du = self.torch.empty((self.D, self.N), dtype=self.torch.float64, device=self.device)
+        elbm_equilibrium_vjp(self.h, rho, u, g, drho, du)
+        return drho, du
 
 
 # ----------------------------------------------------------------------------
