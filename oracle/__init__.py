@@ -44,7 +44,7 @@ _SRC = os.path.join(_HERE, "elbm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libelbm_oracle.so")
 
-MODE_HIGHER, MODE_LOWER, MODE_LBGK = 0, 1, 2
+MODE_HIGHER, MODE_LOWER, MODE_LBGK, MODE_ITERATE1 = 0, 1, 2, 3
 BRANCH_CUTOFF, BRANCH_SOLVED, BRANCH_CLAMPED = 0, 1, 2
 B_DERIVED, B_PRINTED = 0, 1
 CUTOFF = 1e-3

@@ -31,7 +31,11 @@
  *      path length still exceeds alpha_max (only possible when alpha_max < 1),
  *      alpha = alpha_max/2;
  *  R7  with the cutoff disabled, a node with x == 0 exactly (all sums zero)
- *      takes the near-equilibrium limit alpha = 2.
+ *      takes the near-equilibrium limit alpha = 2;
+ *  R12 alpha_Iterate1 (Sec. IV) keeps alpha_Lower where its Newton step cannot
+ *      be taken: 1 + alpha_Lower x_i <= 0 for some i (the mirror state at
+ *      alpha_Lower is not positive, so its entropy is undefined) or
+ *      dF/dalpha <= 0 there.
  */
 #include <math.h>
 #include <stdint.h>
@@ -44,7 +48,7 @@
 #define OR_QMAX 27
 #define OR_CUTOFF 1e-3
 
-enum { OR_MODE_HIGHER = 0, OR_MODE_LOWER = 1, OR_MODE_LBGK = 2 };
+enum { OR_MODE_HIGHER = 0, OR_MODE_LOWER = 1, OR_MODE_LBGK = 2, OR_MODE_ITERATE1 = 3 };
 enum { OR_BRANCH_CUTOFF = 0, OR_BRANCH_SOLVED = 1, OR_BRANCH_CLAMPED = 2 };
 
 /* ------------------------------------------------------------------------ */
@@ -151,6 +155,9 @@ static double or_root(double a, double b, double c)
     return 2.0 * c / (b + sqrt(b * b - 4.0 * a * c));
 }
 
+double or_alpha_iterate1(int Q, const double *f, const double *feq, double alpha_lower);
+static double or_dF(int Q, const double *f, const double *x, double alpha);
+
 int or_alpha(int Q, const double *f, const double *feq, double beta, int cutoff,
              int b_variant, int mode, or_alpha_info *out)
 {
@@ -206,6 +213,13 @@ int or_alpha(int Q, const double *f, const double *feq, double beta, int cutoff,
             r.alpha_lower = aL;
             if (mode == OR_MODE_LOWER) {
                 r.alpha = aL;
+            } else if (mode == OR_MODE_ITERATE1) {
+                /* Sec. IV: one Newton step of Eq. deltaH_ from alpha_Lower (R12). */
+                int ok = 1;
+                for (i = 0; i < Q; i++)
+                    if (1.0 + aL * x[i] <= 0.0) ok = 0;
+                if (ok && or_dF(Q, f, x, aL) <= 0.0) ok = 0;
+                r.alpha = ok ? or_alpha_iterate1(Q, f, feq, aL) : aL;
             } else {
                 double b = 0.0, c = 0.0, a2 = 0.0, a = 0.0, h;
                 double k = (b_variant == 1) ? aL : aL * beta; /* R3 */

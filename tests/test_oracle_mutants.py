@@ -49,7 +49,12 @@ MUTANTS = {
                            [P + "::test_equilibrium_has_the_prescribed_moments"]),
     "upsilon_sign": ("Y[a] = 2.0 - s;", "Y[a] = 2.0 + s - 2.0 * s * s + 1.0;",
                      [P + "::test_equilibrium_has_the_prescribed_moments"]),
-    "stream_direction": ("or_wrap(xx - c[i * D + 0], nx)", "or_wrap(xx + c[i * D + 0], nx)",
+    "stream_direction": ("or_wrap(xx - c[i * D + 0], nx);\n                    int64_t sy = or_wrap(y - c[i * D + 1], ny);\n"
+                         "                    int64_t sz = (D == 3) ? or_wrap(z - c[i * D + 2], nz) : 0;\n"
+                         "                    fout",
+                         "or_wrap(xx + c[i * D + 0], nx);\n                    int64_t sy = or_wrap(y - c[i * D + 1], ny);\n"
+                         "                    int64_t sz = (D == 3) ? or_wrap(z - c[i * D + 2], nz) : 0;\n"
+                         "                    fout",
                          [F + "::test_stream_moves_along_velocity"]),
     "clamp_rule": ("r.alpha = (1.0 + r.alpha_max) / 2.0;", "r.alpha = r.alpha_max;",
                    [P + "::test_positivity_clamp"]),

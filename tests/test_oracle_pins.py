@@ -583,3 +583,37 @@ def test_table1_magnitudes_on_synthetic_states():
         a, _, _ = O.alpha_elbm(f, feq, 2.0)
         gap = (4.0 / 3.0) * (beta ** 2 - 1) * np.sum(f * x ** 3) / np.sum(f * x ** 2)
         assert abs((info.alpha_higher - a) - gap) < 30 * np.max(np.abs(x)) ** 2
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_iterate1_mode_of_the_collision(D):
+    """Sec. IV: the collision's alpha_Iterate1 mode is one Newton step of the mirror-state
+    equation from alpha_Lower.  F is convex in alpha and increasing past its minimum at
+    alpha ~ 1, so a Newton step from alpha_Lower < alpha_ELBM overshoots: alpha_ELBM <=
+    alpha_Iterate1, closer to alpha_ELBM than alpha_Lower; the cutoff and the positivity
+    clamp apply to it as to the other modes; the entropy does not decrease to first order."""
+    rng = np.random.default_rng(181 + D)
+    beta = 0.98
+    for _ in range(150):
+        f = near_eq_state(rng, D, 10 ** rng.uniform(-3.5, -1.5))
+        feq, x = with_eq(D, f)
+        lo = O.alpha(f, feq, beta, cutoff=False, mode=O.MODE_LOWER)
+        it = O.alpha(f, feq, beta, cutoff=False, mode=O.MODE_ITERATE1)
+        a, _, st = O.alpha_elbm(f, feq, 2.0)
+        assert st == 0 and it.branch == O.BRANCH_SOLVED
+        assert it.alpha == O.alpha_iterate1(f, feq, lo.alpha_lower)
+        assert lo.alpha_lower <= a + 1e-12
+        assert a - 1e-12 * a <= it.alpha
+        assert abs(it.alpha - a) <= abs(lo.alpha_lower - a) + 1e-13
+        # with the cutoff on, states inside it keep alpha = 2
+        if np.max(np.abs(x)) < O.CUTOFF:
+            c = O.alpha(f, feq, beta, cutoff=True, mode=O.MODE_ITERATE1)
+            assert c.alpha == 2.0 and c.branch == O.BRANCH_CUTOFF
+    # far from equilibrium: where 1 + alpha_L x_min <= 0 the Newton step is undefined and
+    # alpha_L is kept (R12), then clamped like every other mode
+    f = O.equilibrium(D, 1.0, np.full(D, 0.05)) * np.r_[np.full(3 ** D - 1, 1.0), 9.0]
+    feq, x = with_eq(D, f)
+    lo = O.alpha(f, feq, beta, cutoff=True, mode=O.MODE_LOWER)
+    it = O.alpha(f, feq, beta, cutoff=True, mode=O.MODE_ITERATE1)
+    assert 1.0 + lo.alpha_lower * x.min() <= 0.0
+    assert it.alpha == lo.alpha and it.branch == lo.branch
