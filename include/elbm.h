@@ -72,10 +72,15 @@ extern "C" {
 #define ELBM_STORE_BF16DEV 3
 
 /* Path-length rule.  HIGHER is the paper's alpha_Higher (default); LOWER the
- * more dissipative alpha_Lower (Sec. III A); LBGK the constant alpha = 2. */
+ * more dissipative alpha_Lower (Sec. III A); LBGK the constant alpha = 2;
+ * ITERATE1 one Newton step of the mirror-state entropy equation (Eq. deltaH_)
+ * started from alpha_Lower, the alpha_Iterate1 of Sec. IV (Table III) -- a
+ * comparison variant that evaluates logarithms, off the FP32 fast path.  The
+ * cutoff and the positivity clamp apply to every rule but LBGK. */
 #define ELBM_ALPHA_HIGHER 0
 #define ELBM_ALPHA_LOWER 1
 #define ELBM_ALPHA_LBGK 2
+#define ELBM_ALPHA_ITERATE1 3
 
 /* Reading of the Omega+ denominators in the b coefficient (Eq.
  * qaud_tight_coeff): DERIVED uses 4 + m alpha_Lower beta x (m = 1, 2, 3), as
@@ -89,7 +94,7 @@ extern "C" {
  * row of an x-row in shared memory with bulk asynchronous copies (TMA engine,
  * mbarrier pipeline); needs FP32 or 16-bit storage, nx * element size a
  * multiple of 16 bytes and nx <= 1024 (D2Q9) or 512 (D3Q27).  AUTO (default)
- * takes ROWS when it applies, else DIRECT.  Both kernels evaluate the same
+ * takes DIRECT, the faster of the two on GB300.  Both kernels evaluate the same
  * per-node arithmetic; they agree to rounding (the compiler may fuse
  * multiply-adds differently in each). */
 #define ELBM_KERNEL_AUTO 0
@@ -207,6 +212,13 @@ int elbm_moments(elbm_t *h, double *rho_out, double *u_out, int where);
  * doubles; flags_out: N bytes of ELBM_BRANCH_* (may be NULL).  Both in the
  * same memory space (where).  Host outputs synchronise the stream. */
 int elbm_alpha_field(elbm_t *h, double *alpha_out, uint8_t *flags_out, int where);
+
+/* Subgrid (turbulent) viscosity implied by the path length of the next
+ * collision at every node, nu_T = theta dt (2 - alpha) / (2 alpha beta) with
+ * theta = 1/3, dt = 1 (Sec. VI, Eq. nuT): positive where alpha < 2 adds
+ * dissipation, negative where alpha > 2 removes it.  nut_out: N doubles in
+ * memory space `where`.  Host output synchronises the stream. */
+int elbm_subgrid_viscosity(elbm_t *h, double *nut_out, int where);
 
 /* Domain-wide diagnostics: mass, momentum and H of the current state, and the
  * alpha statistics, per-node entropy change H[f*] - H[f] (Eq. deltaH3, FP64)

@@ -42,43 +42,65 @@ __device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin)[Lattice<D>:
     constexpr int Q = Lattice<D>::Q;
     const T beta = T(p.beta);
 
-    // ---- forward: moments and the product-form equilibrium (Sec. I) ----
-    T rho = T(0), j[D];
+    // ---- forward: moments and the equilibrium (Sec. I), in the forms the step uses ----
+    // Deviations from k_i T(W) (exact), drho corrected for the rest of W, r = rho W in two
+    // parts, and per axis eps(c) = -t, 2t +- 3u with t = s - 1 = 3u^2/(1+s): then
+    // f^eq_i = k_i r (1 + E_i) and f^eq_i - F_i = (k_i r) E_i + (k_i r - F_i) with one
+    // rounding.  The same care matters here as in the step: a VJP of f^eq built on
+    // rounded weights maps the conserved adjoint modes (g_i = a + c_i . m) to (1 + e)
+    // times themselves, and e ~ 1e-8 per step grows over a long reverse sweep.
+    T dev[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dev[i] = F[i] - T(weight_k(D, i)) * T(weight_unit(D));
+    T drho = T(0), j[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) j[a] = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        rho += F[i];
+        drho += dev[i];
 #pragma unroll
-        for (int a = 0; a < D; ++a) j[a] += T(vel(D, i, a)) * F[i];
+        for (int a = 0; a < D; ++a) j[a] += T(vel(D, i, a)) * dev[i];
     }
-    T u[D], phi[D][3], dlp[D][3];
+    drho -= T(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, T>()));
+    const T rho = T(1) + drho;
+    const T irho = T(1) / rho;
+    const T rW = fma(rho, T(weight_unit(D)), rho * weight_unit_lo<D, T>());
+    // eps[a][c+1] and its derivative d eps / d u_a: 6u/s - 3, -3u/s, 6u/s + 3
+    T u[D], eps[D][3], deps[D][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        u[a] = j[a] / rho;
-        const T s = sqrt(T(1) + T(3) * u[a] * u[a]);
-        const T Y = T(2) - s;
-        const T num = T(2) * u[a] + s, den = T(1) - u[a];
-        const T z = num / den;
-        const T dY = -T(3) * u[a] / s;                                 // dUpsilon/du
-        const T dlz = (T(2) + T(3) * u[a] / s) / num + T(1) / den;    // d log z / du
-        phi[a][0] = Y / (T(6) * z);
-        phi[a][1] = Y * T(4.0 / 6.0);
-        phi[a][2] = Y * z / T(6);
-        dlp[a][0] = dY / Y - dlz;
-        dlp[a][1] = dY / Y;
-        dlp[a][2] = dY / Y + dlz;
+        u[a] = j[a] * irho;
+        const T sq = sqrt(T(1) + T(3) * u[a] * u[a]);
+        const T t = T(3) * u[a] * u[a] / (T(1) + sq);
+        eps[a][0] = T(2) * t - T(3) * u[a];
+        eps[a][1] = -t;
+        eps[a][2] = T(2) * t + T(3) * u[a];
+        const T v = T(3) * u[a] / sq;
+        deps[a][0] = T(2) * v - T(3);
+        deps[a][1] = -v;
+        deps[a][2] = T(2) * v + T(3);
     }
-    T feq[Q], x[Q];
+    // E without axis `skip` (skip = D: all axes): prod (1 + eps) - 1, never rounding 1 + eps
+    auto E_excl = [&](int i, int skip) -> T {
+        T e = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (a != skip) {
+                const T ea = eps[a][vel(D, i, a) + 1];
+                e = e + ea + e * ea;
+            }
+        return e;
+    };
+    T feq[Q], x[Q], delta[Q];
     T xabs = T(0), xmin = T(0);
     int imin = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        T v = rho;
-#pragma unroll
-        for (int a = 0; a < D; ++a) v *= phi[a][vel(D, i, a) + 1];
-        feq[i] = v;
-        x[i] = v / F[i] - T(1);
+        const T kr = T(weight_k(D, i)) * rW;
+        const T E = E_excl(i, D);
+        delta[i] = fma(kr, E, kr - F[i]);
+        feq[i] = F[i] + delta[i];
+        x[i] = delta[i] / F[i];
         xabs = fmax(xabs, fabs(x[i]));
         if (x[i] < xmin) {
             xmin = x[i];
@@ -209,34 +231,40 @@ __device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin)[Lattice<D>:
             }
         }
     }
-    // x_i = feq_i / F_i - 1 and the equilibrium's dependence on F through (rho, u)
+    // x_i = f^eq_i / F_i - 1 and the equilibrium's dependence on F through (rho, u)
     T lam[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         Fb[i] += -xb[i] * feq[i] / (F[i] * F[i]);
         lam[i] = xb[i] / F[i];
     }
-    // VJP of f^eq: sum_i l_i d feq_i / d F_j = G_rho + sum_a G_a (c_ja - u_a) / rho
+    // VJP of f^eq = rho W k_i prod_a (1 + eps_a(c_ia)), u = j / rho:
+    //   sum_i l_i d feq_i / d F_j = G_rho + sum_a G_a (c_ja - u_a) / rho,
+    //   G_rho = sum_i l_i feq_i / rho,
+    //   G_a = sum_i l_i (k_i r) eps_a'(c_ia) prod_{b != a} (1 + eps_b(c_ib)).
     auto feq_vjp = [&](const T (&l)[Q], T (&out)[Q]) {
         T Gr = T(0), Ga[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) Ga[a] = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const T lf = l[i] * feq[i];
-            Gr += lf;
+            Gr += l[i] * feq[i];
+            const T lk = l[i] * (T(weight_k(D, i)) * rW);
 #pragma unroll
-            for (int a = 0; a < D; ++a) Ga[a] += lf * dlp[a][vel(D, i, a) + 1];
+            for (int a = 0; a < D; ++a) {
+                const T q = lk * deps[a][vel(D, i, a) + 1];
+                Ga[a] += fma(q, E_excl(i, a), q);
+            }
         }
-        Gr /= rho;
+        Gr *= irho;
         T base = Gr;
 #pragma unroll
-        for (int a = 0; a < D; ++a) base -= Ga[a] * u[a] / rho;
+        for (int a = 0; a < D; ++a) base -= Ga[a] * u[a] * irho;
 #pragma unroll
         for (int jj = 0; jj < Q; ++jj) {
             T v = base;
 #pragma unroll
-            for (int a = 0; a < D; ++a) v += Ga[a] * T(vel(D, jj, a)) / rho;
+            for (int a = 0; a < D; ++a) v += Ga[a] * T(vel(D, jj, a)) * irho;
             out[jj] = v;
         }
     };
@@ -248,7 +276,7 @@ __device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin)[Lattice<D>:
     // ---- the collision's VJP: h_j = g_j + beta (s dalpha/dF_j + alpha (feq_vjp(g)_j - g_j)) ----
     T s = T(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) s += gin[i] * (feq[i] - F[i]);
+    for (int i = 0; i < Q; ++i) s += gin[i] * delta[i];
     feq_vjp(gin, V);
 #pragma unroll
     for (int i = 0; i < Q; ++i) h[i] = gin[i] + beta * (s * Fb[i] + alpha * (V[i] - gin[i]));

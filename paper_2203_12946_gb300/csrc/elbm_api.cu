@@ -205,7 +205,7 @@ int elbm_create(elbm_t **out, int lattice, const int64_t dims[3], double beta, i
     elbm_default_opts(&o);
     if (opts) o = *opts;
     if (!storage_size(o.storage)) return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown storage %d", o.storage);
-    if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_LBGK)
+    if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_ITERATE1)
         return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown alpha_mode %d", o.alpha_mode);
     if (o.b_variant != ELBM_B_DERIVED && o.b_variant != ELBM_B_PRINTED)
         return fail(nullptr, ELBM_ERR_ARG, "elbm_create: unknown b_variant %d", o.b_variant);
@@ -435,7 +435,7 @@ int elbm_alpha_field(elbm_t *h, double *alpha_out, uint8_t *flags_out, int where
         df = flags_out ? reinterpret_cast<uint8_t *>(h->stage + N) : nullptr;
     }
     cudaError_t e = ELBM_BY_LATTICE(h, launch_alpha, h->opts.storage, h->pop[h->cur], h->g, params_of(h), da, df,
-                                    h->stream);
+                                    nullptr, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "elbm_alpha_field: kernel launch");
     if (where == ELBM_MEM_HOST) {
         e = cudaMemcpyAsync(alpha_out, da, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -446,6 +446,32 @@ int elbm_alpha_field(elbm_t *h, double *alpha_out, uint8_t *flags_out, int where
         }
         e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "elbm_alpha_field: synchronize");
+    }
+    return ELBM_OK;
+}
+
+int elbm_subgrid_viscosity(elbm_t *h, double *nut_out, int where)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_subgrid_viscosity: handle is NULL");
+    if (!nut_out) return fail(h, ELBM_ERR_ARG, "elbm_subgrid_viscosity: nut_out is NULL");
+    if (where != ELBM_MEM_DEVICE && where != ELBM_MEM_HOST)
+        return fail(h, ELBM_ERR_ARG, "elbm_subgrid_viscosity: bad memory location %d", where);
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_subgrid_viscosity: no state");
+    DeviceGuard guard(h->opts.device);
+    const int64_t N = h->g.N;
+    double *dn = nut_out;
+    int st;
+    if (where == ELBM_MEM_HOST) {
+        if ((st = ensure_stage(h, size_t(N) * sizeof(double))) != ELBM_OK) return st;
+        dn = h->stage;
+    }
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_alpha, h->opts.storage, h->pop[h->cur], h->g, params_of(h), nullptr,
+                                    nullptr, dn, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_subgrid_viscosity: kernel launch");
+    if (where == ELBM_MEM_HOST) {
+        e = cudaMemcpyAsync(nut_out, dn, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_subgrid_viscosity: read back");
     }
     return ELBM_OK;
 }

@@ -203,7 +203,7 @@ int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64
     if (opts) o = *opts;
     const size_t es = elem_size(o.storage);
     if (!es) return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_create: unknown storage %d", o.storage);
-    if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_LBGK || (o.cutoff != 0 && o.cutoff != 1) ||
+    if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_ITERATE1 || (o.cutoff != 0 && o.cutoff != 1) ||
         (o.b_variant != ELBM_B_DERIVED && o.b_variant != ELBM_B_PRINTED) || !(o.rho0 > 0.0))
         return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_create: invalid options");
     const int Q = lattice;

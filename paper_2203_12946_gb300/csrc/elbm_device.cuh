@@ -39,6 +39,23 @@ __host__ __device__ constexpr double weight(int D, int i)
     return w;
 }
 
+// Every weight is a power of two times W = 6^-D: w_i = k_i W, k_i in {1, 4, 16, 64}
+// (Sec. I, products of the D1Q3 weights 1/6, 4/6, 1/6).  In floating point
+// k_i T(W) is then exactly T(w_i), and with r = rho W formed once per node,
+// k_i r = w_i rho up to one rounding of r shared by every population.
+__host__ __device__ constexpr double weight_unit(int D) { return D == 2 ? 1.0 / 36.0 : 1.0 / 216.0; }
+__host__ __device__ constexpr double weight_k(int D, int i)
+{
+    double k = 1.0;
+    for (int a = 0; a < D; ++a) k *= (vel(D, i, a) == 0 ? 4.0 : 1.0);
+    return k;
+}
+template <int D, class T>
+__host__ __device__ constexpr T weight_unit_lo()
+{
+    return T(weight_unit(D) - double(T(weight_unit(D))));
+}
+
 // Sum of the weights after rounding to T, minus one (zero in exact arithmetic).
 template <int D, class T>
 __host__ __device__ constexpr double weight_sum_error()
@@ -56,7 +73,7 @@ struct Geometry {
 // Near-equilibrium cutoff of Appendix D (strict test |x|max < 1e-3).
 constexpr double kCutoff = 1e-3;
 
-enum { kModeHigher = 0, kModeLower = 1, kModeLBGK = 2 };
+enum { kModeHigher = 0, kModeLower = 1, kModeLBGK = 2, kModeIterate1 = 3 };
 enum { kBranchCutoff = 0, kBranchSolved = 1, kBranchClamped = 2 };
 
 struct CollideParams {
@@ -81,6 +98,18 @@ __device__ __forceinline__ float rcp_(float b)
     return r;
 }
 __device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
+// 1/rho for the velocity u = j/rho: the approximate reciprocal followed by one
+// Newton-Raphson step for 1/b (r + r (1 - b r)).  The approximation alone is off
+// by a fraction of an ulp with the same sign for every rho near 1, which scales
+// the equilibrium momentum by the same factor at every node and step and builds
+// up in long runs (FP32 kinetic energy drifted by 5e-5 in 2000 steps at
+// beta = 0.9); after the step the error is a rounding error with no preferred sign.
+__device__ __forceinline__ float rcp_nr(float b)
+{
+    const float r = rcp_(b);
+    return fmaf(r, fmaf(-b, r, 1.0f), r);
+}
+__device__ __forceinline__ double rcp_nr(double b) { return 1.0 / b; }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 // FP32 square roots on the path act on 1 + O(u^2) and 1 - 4pq >= 1: the
 // approximate instruction (relative error ~2^-23) loses nothing there.
@@ -148,6 +177,9 @@ struct StoreBF16Dev {
     }
 };
 
+template <class T>
+__device__ __forceinline__ T g_entropy(T y);
+
 // ---------------------------------------------------------------------------
 // Positive root of -alpha^2 a + alpha b - c in the conjugate form of Eq.
 // alphaLowerSoln, 2c / (b + sqrt(b^2 - 4ac)), evaluated with b factored out,
@@ -175,9 +207,13 @@ __device__ __forceinline__ T quad_root(T a, T b, T c)
 //    rho = 1 + drho, and per axis eps(c) = Upsilon z^c - 1 (c = -1, 0, 1),
 //    f^eq_i - f_i = w_i (drho + rho E_i) - d_i,  E_i = prod_a (1 + eps_a(c_ia)) - 1,
 //    so no rounding happens at the scale of w_i (FP32 keeps ~u times more
-//    digits of f^eq - f than the product form evaluated directly).  The axis
-//    factors use Upsilon - 1 = -3u^2/(1+s), z - 1 = (3u + 3u^2/(1+s))/(1-u) and
-//    1/z - 1 = -(3u + 3u^2/(1+s))/(2u+s), s = sqrt(1 + 3u^2).
+//    digits of f^eq - f than the product form evaluated directly).  The
+//    difference itself is formed as (k_i r) E_i + (k_i r - f_i) with
+//    w_i = k_i W, r = rho W (see below), rounded once.  With
+//    s = sqrt(1 + 3u^2) and t = s - 1 = 3u^2/(1+s), the axis factors reduce
+//    exactly to Upsilon - 1 = -t and Upsilon z^{+-1} - 1 = 2t +- 3u (since
+//    (2-s)(2u+s) = (1-u)(2s-1+3u) and 1/z(u) = z(-u)): one reciprocal per axis,
+//    and the first moment (eps(+1) - eps(-1))/6 = u carries no bias from it.
 //  * The Gauss-Legendre denominator factors: 60 + 90x + 36x^2 + 3x^3 =
 //    (2 + x)(30 + 30x + 3x^2), so the c1 and c terms share one reciprocal.
 //  * The Omega+ bracket 2/(4+t) + 1/(4+2t) + 2/(4+3t) is the single rational
@@ -198,7 +234,7 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
     // along the last axis first, then the middle, then the first.
     T dev[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) dev[i] = f[i] - T(weight(D, i));
+    for (int i = 0; i < Q; ++i) dev[i] = f[i] - T(weight_k(D, i)) * T(weight_unit(D)); // exact
     constexpr int P = Q / 3; // columns along the last axis
     T s0[P], s1[P];          // per column: sum over c_last, and (c_last=+1) - (c_last=-1)
 #pragma unroll
@@ -224,30 +260,33 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
         j[1] = ty[0] + ty[1] + ty[2];
         j[D - 1] = tz[0] + tz[1] + tz[2];
     }
-    // rho = 1 + drho.  The weights rounded to T sum to 1 + e_w (|e_w| ~ 1e-8 in
-    // FP32); building f^eq on those same weights with 1 + drho gives it the mass
-    // (1 + drho)(1 + e_w) = sum f + drho e_w, so e_w must not be added to drho.
+    // The deviations were taken from k_i T(W); the rest of W (sum k_i = 6^D) is
+    // taken off drho, so rho = sum f to rounding.  r = rho W in two parts.
+    drho -= T(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, T>()));
     const T rho = T(1) + drho;
-    const T irho = div_(T(1), rho);
+    const T r = fma(rho, T(weight_unit(D)), rho * weight_unit_lo<D, T>());
+    const T irho = rcp_nr(rho);
 
-    // Per axis eps(c) = Upsilon z^c - 1 for c = -1, 0, +1 (Sec. I equilibrium).
+    // Per axis eps(c) = Upsilon z^c - 1 for c = -1, 0, +1 (Sec. I equilibrium),
+    // in the reduced form -t, 2t +- 3u.
     T eps[D][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const T u = j[a] * irho;
         const T s = sqrt_(T(1) + T(3) * u * u);
-        // O(u) quantities: a 2-ulp reciprocal changes them by 2 ulp of themselves
-        const T sm1 = div_(T(3) * u * u, T(1) + s);  // s - 1
-        const T num = T(3) * u + sm1;                // (2u + s) - (1 - u)
-        const T zm1 = div_(num, T(1) - u);           // z - 1
-        const T zim1 = -div_(num, T(2) * u + s);     // 1/z - 1
-        const T e0 = -sm1;                             // Upsilon - 1
-        eps[a][0] = e0 + zim1 + e0 * zim1;
-        eps[a][1] = e0;
-        eps[a][2] = e0 + zm1 + e0 * zm1;
+        const T t = div_(T(3) * u * u, T(1) + s); // s - 1, without cancellation
+        eps[a][0] = T(2) * t - T(3) * u;          // Upsilon / z - 1
+        eps[a][1] = -t;                           // Upsilon - 1
+        eps[a][2] = T(2) * t + T(3) * u;          // Upsilon z - 1
     }
 
-    // x_i = (f^eq_i - f_i) / f_i with f^eq_i - f_i = w_i (drho + rho E_i) - d_i.
+    // x_i = (f^eq_i - f_i) / f_i with f^eq_i - f_i = (k_i r) E_i + (k_i r - f_i): k_i r
+    // is exact (a power of two times r) and so is k_i r - f_i wherever f_i is within
+    // a factor two of f^eq_i (Sterbenz), leaving one rounding, at the scale of
+    // f^eq - f.  Forming w_i (drho + rho E_i) - d_i instead rounds at the scale of
+    // w_i u and with the rounded w_i, which in FP32 biased the momentum of f^eq by
+    // ~3e-8 of itself per step (the kinetic energy of a decaying D2Q9 vortex,
+    // beta = 0.9, 8e-5 above FP64 after 2000 steps).
     T xabs = T(0), xmin = T(0);
     T fx[Q];
 #pragma unroll
@@ -265,7 +304,8 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
             const int i = 3 * k + c;
             const T el = eps[D - 1][c];
             const T E = A + el + A * el;
-            const T delta = T(weight(D, i)) * (drho + rho * E) - dev[i];
+            const T kr = T(weight_k(D, i)) * r;
+            const T delta = fma(kr, E, kr - f[i]);
             x[i] = div_(delta, f[i]);
             fx[i] = delta; // f_i x_i, reused by the sums below
             xabs = fmax(xabs, fabs(x[i]));
@@ -305,6 +345,23 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
             const T aL = quad_root(T(0.5) * S3, b1, c1);
             if (p.mode == kModeLower) {
                 alpha = aL;
+            } else if (p.mode == kModeIterate1) {
+                // alpha_Iterate1 (Sec. IV): one Newton step of the mirror-state equation
+                // H[f + alpha (f^eq - f)] = H[f] (Eq. deltaH_) from alpha_Lower:
+                // F(a) = <f, g(a x)> - a <f, x log(1+x)> with g(y) = (1+y) log(1+y) - y
+                // (using <f,x> = 0), F'(a) = <f, x (log(1+a x) - log(1+x))>.  Where the
+                // step is undefined (some 1 + aL x_i <= 0) or F'(aL) <= 0, aL is kept.
+                T Fv = T(0), dF = T(0);
+                bool ok = true;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const T xi = x[i];
+                    ok = ok && (T(1) + aL * xi > T(0));
+                    const T l1 = log1p(xi), la = log1p(aL * xi);
+                    Fv += f[i] * (g_entropy<T>(aL * xi) - aL * xi * l1);
+                    dF += f[i] * xi * (la - l1);
+                }
+                alpha = (ok && dF > T(0)) ? aL - Fv / dF : aL;
             } else {
                 // b of Eq. qaud_tight_coeff, k = alpha_L beta (derived) or alpha_L (printed).
                 const T k = p.b_variant ? aL : aL * beta;
@@ -377,11 +434,16 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
 __device__ __forceinline__ float2 prcp(float2 a) { return f2(rcp_(a.x), rcp_(a.y)); }
 
-// Weight pair of pair k (0 in the padding lane).
+// Weight pair of pair k, as k_i T(W) (0 in the padding lane), and the k_i pair.
 template <int D>
 __host__ __device__ constexpr float wpair(int k, int lane)
 {
-    return (2 * k + lane) < Lattice<D>::Q ? float(weight(D, 2 * k + lane)) : 0.0f;
+    return (2 * k + lane) < Lattice<D>::Q ? float(weight_k(D, 2 * k + lane)) * float(weight_unit(D)) : 0.0f;
+}
+template <int D>
+__host__ __device__ constexpr float kpair(int k, int lane)
+{
+    return (2 * k + lane) < Lattice<D>::Q ? float(weight_k(D, 2 * k + lane)) : 0.0f;
 }
 
 template <int D, bool kRelax = true>
@@ -424,8 +486,10 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         j[1] = ty[0] + ty[1] + ty[2];
         j[D - 1] = tz[0] + tz[1] + tz[2];
     }
+    drho -= float(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, float>())); // as in node_collide
     const float rho = 1.0f + drho;
-    const float irho = rcp_(rho);
+    const float irho = rcp_nr(rho);
+    const float r = fmaf(rho, float(weight_unit(D)), rho * weight_unit_lo<D, float>());
 
     // Per axis eps(c) = Upsilon z^c - 1 (as in node_collide).
     float eps[D][3];
@@ -433,14 +497,10 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
     for (int a = 0; a < D; ++a) {
         const float u = j[a] * irho;
         const float s = sqrt_(1.0f + 3.0f * u * u);
-        const float sm1 = div_(3.0f * u * u, 1.0f + s);
-        const float num = 3.0f * u + sm1;
-        const float zm1 = div_(num, 1.0f - u);
-        const float zim1 = -div_(num, 2.0f * u + s);
-        const float e0 = -sm1;
-        eps[a][0] = e0 + zim1 + e0 * zim1;
-        eps[a][1] = e0;
-        eps[a][2] = e0 + zm1 + e0 * zm1;
+        const float t = div_(3.0f * u * u, 1.0f + s);
+        eps[a][0] = 2.0f * t - 3.0f * u;
+        eps[a][1] = -t;
+        eps[a][2] = 2.0f * t + 3.0f * u;
     }
     // E_i = prod_a (1 + eps_a(c_ia)) - 1, per population.
     auto E_of = [&](int i) -> float {
@@ -456,8 +516,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         return A + el + A * el;
     };
 
-    // x_i = (f^eq_i - f_i) / f_i with f^eq_i - f_i = w_i (drho + rho E_i) - d_i, and in
-    // the same pass the x-only sums of Eq. alphaLowerCoeffs / qaud_tight_coeff and the
+    // x_i = (f^eq_i - f_i) / f_i, and in the same pass the x-only sums of Eq. alphaLowerCoeffs / qaud_tight_coeff and the
     // Omega- power sums (wasted only where the whole warp ends on the cutoff branch).
     float xabs = 0.0f, xmin = 0.0f;
     float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f);
@@ -465,7 +524,9 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const float2 E = f2(E_of(2 * k), E_of(2 * k + 1));
-        float2 delta = psub(pmul(f2(wpair<D>(k, 0), wpair<D>(k, 1)), pfma(f2(rho), E, f2(drho))), dp[k]);
+        // f^eq - f = (k_i r) E_i + (k_i r - f_i), one rounding (as in node_collide)
+        const float2 kr = pmul(f2(kpair<D>(k, 0), kpair<D>(k, 1)), f2(r));
+        float2 delta = pfma(kr, E, psub(kr, fp[k]));
         if (kPad && k == NP - 1) delta.y = 0.0f; // padding lane: f = 1, x = 0
         const float2 xi = pmul(delta, prcp(fp[k]));
         xp[k] = xi;
@@ -546,6 +607,8 @@ __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q
 {
     constexpr int Q = Lattice<D>::Q;
     if constexpr (sizeof(T) == 4) {
+        // alpha_Iterate1 (a comparison variant with logarithms) stays on the scalar path
+        if (p.mode == kModeIterate1) return node_collide<D, T, kRelax>(f, x, p, branch);
         constexpr int NP = Pairs<D>::NP;
         float2 fp[NP], xp[NP];
 #pragma unroll

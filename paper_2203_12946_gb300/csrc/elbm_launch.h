@@ -60,7 +60,7 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
                                         double *rho_out, double *u_out, cudaStream_t s);            \
     cudaError_t launch_alpha_##SUFFIX(int storage, const void *f, const Geometry &g,                \
                                       const CollideParams &p, double *alpha_out, uint8_t *flags,    \
-                                      cudaStream_t s);                                               \
+                                      double *nut_out, cudaStream_t s);                              \
     cudaError_t launch_diag_##SUFFIX(int storage, const void *f, const Geometry &g,                 \
                                      const CollideParams &p, DiagAcc *acc, int num_sms,             \
                                      cudaStream_t s);                                                \

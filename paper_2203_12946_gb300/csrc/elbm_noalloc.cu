@@ -80,7 +80,7 @@ extern "C" int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], doub
     if (opts) o = *opts;
     if (o.storage < ELBM_STORE_F64 || o.storage > ELBM_STORE_BF16DEV)
         return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: unknown storage %d", o.storage);
-    if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_LBGK || (o.cutoff != 0 && o.cutoff != 1) ||
+    if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_ITERATE1 || (o.cutoff != 0 && o.cutoff != 1) ||
         (o.b_variant != ELBM_B_DERIVED && o.b_variant != ELBM_B_PRINTED) || !(o.rho0 > 0.0))
         return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: invalid options");
     // The scratch this call needs must fit the fixed array.

@@ -30,7 +30,7 @@ ELBM_D2Q9 = 9
 ELBM_D3Q27 = 27
 ELBM_BC_PERIODIC = 0
 ELBM_STORE_F64, ELBM_STORE_F32, ELBM_STORE_F16DEV, ELBM_STORE_BF16DEV = 0, 1, 2, 3
-ELBM_ALPHA_HIGHER, ELBM_ALPHA_LOWER, ELBM_ALPHA_LBGK = 0, 1, 2
+ELBM_ALPHA_HIGHER, ELBM_ALPHA_LOWER, ELBM_ALPHA_LBGK, ELBM_ALPHA_ITERATE1 = 0, 1, 2, 3
 ELBM_B_DERIVED, ELBM_B_PRINTED = 0, 1
 ELBM_MEM_DEVICE, ELBM_MEM_HOST = 0, 1
 ELBM_KERNEL_AUTO, ELBM_KERNEL_DIRECT, ELBM_KERNEL_ROWS = 0, 1, 2
@@ -50,7 +50,8 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
             "elbm_batch_create", "elbm_batch_destroy", "elbm_batch_last_error", "elbm_batch_info",
             "elbm_batch_init_equilibrium", "elbm_batch_step", "elbm_batch_tune", "elbm_batch_moments",
             "elbm_batch_diagnostics", "elbm_batch_get_populations", "elbm_batch_set_populations",
-            "elbm_batch_synchronize", "elbm_adjoint_step", "elbm_kinetic_energy", "elbm_equilibrium_vjp"]
+            "elbm_batch_synchronize", "elbm_adjoint_step", "elbm_kinetic_energy", "elbm_equilibrium_vjp",
+            "elbm_subgrid_viscosity"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -140,6 +141,7 @@ def load(build_if_missing: bool = True):
             "elbm_adjoint_step": (ctypes.c_int, [P, P, P, P]),
             "elbm_kinetic_energy": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_double), P]),
             "elbm_equilibrium_vjp": (ctypes.c_int, [P, P, P, P, P, P]),
+            "elbm_subgrid_viscosity": (ctypes.c_int, [P, P, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -261,6 +263,10 @@ def elbm_diagnostics_noalloc(lattice, dims, beta, populations, opts: elbm_opts |
     out = d.as_dict()
     out["status"] = code
     return out
+
+
+def elbm_subgrid_viscosity(h, nut_out, where=ELBM_MEM_DEVICE) -> None:
+    _check(h, load().elbm_subgrid_viscosity(h, _ptr(nut_out), int(where)), "elbm_subgrid_viscosity")
 
 
 def elbm_adjoint_step(h, f_t, g_next, g_t) -> None:
@@ -385,6 +391,11 @@ class Simulation:
         fl = torch.empty(self.N, dtype=torch.uint8, device=self.device)
         elbm_alpha_field(self.h, a, fl, ELBM_MEM_DEVICE)
         return a, fl
+
+    def subgrid_viscosity(self):
+        nut = self.torch.empty(self.N, dtype=self.torch.float64, device=self.device)
+        elbm_subgrid_viscosity(self.h, nut, ELBM_MEM_DEVICE)
+        return nut
 
     def diagnostics(self, with_hist=False, allow_nonphysical=False):
         hist = np.zeros(ELBM_HIST_BINS + 2, dtype=np.int64) if with_hist else None

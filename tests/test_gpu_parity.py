@@ -27,7 +27,7 @@ pytestmark = pytest.mark.gpu
 
 LAT = {2: E.ELBM_D2Q9, 3: E.ELBM_D3Q27}
 MODES = {"higher": (E.ELBM_ALPHA_HIGHER, O.MODE_HIGHER), "lower": (E.ELBM_ALPHA_LOWER, O.MODE_LOWER),
-         "lbgk": (E.ELBM_ALPHA_LBGK, O.MODE_LBGK)}
+         "lbgk": (E.ELBM_ALPHA_LBGK, O.MODE_LBGK), "iterate1": (E.ELBM_ALPHA_ITERATE1, O.MODE_ITERATE1)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -85,7 +85,7 @@ def check_branches(D, f_pre, br_gpu, br_ora, band):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("D,dims", [(2, (300, 37, 1)), (3, (37, 19, 11))])
-@pytest.mark.parametrize("mode", ["higher", "lower", "lbgk"])
+@pytest.mark.parametrize("mode", ["higher", "lower", "lbgk", "iterate1"])
 @pytest.mark.parametrize("cutoff", [True, False])
 def test_fp64_single_step_every_node(D, dims, mode, cutoff):
     beta = 0.995
@@ -167,6 +167,49 @@ def test_fp32_single_step(D, dims, cutoff):
     assert np.max(np.abs(a_gpu[agree] - a_ora[agree])) < 2e-5
     rel = np.abs(f_gpu - f_ora) / f_ora
     assert np.max(rel[:, agree]) < 2e-6
+
+
+@pytest.mark.parametrize("D,dims", [(2, (131, 29, 1)), (3, (21, 13, 9))])
+def test_fp32_iterate1_mode(D, dims):
+    """alpha_Iterate1 (Sec. IV) in FP32 against the oracle, including nodes far enough
+    from equilibrium that the Newton step is undefined and alpha_Lower is kept."""
+    beta = 0.99
+    f0 = noisy_state(D, dims, 0.5, seed=8).astype(np.float32)
+    f_in = f0.astype(np.float64)
+    gm, om = MODES["iterate1"]
+    f_gpu = gpu_run(D, dims, beta, f0, 1, "f32", alpha_mode=gm, cutoff=True)
+    f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=True, mode=om, want_alpha=True)
+    with E.Simulation(LAT[D], dims, beta, storage="f32", alpha_mode=gm, cutoff=True) as sim:
+        sim.set_populations(f0)
+        a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]
+    agree = check_branches(D, O.stream(D, dims, f_in), fl, br_ora, 1e-6)
+    assert np.sum(br_ora == O.BRANCH_CLAMPED) > 0 and np.sum(br_ora == O.BRANCH_SOLVED) > 0
+    err = np.abs(a_gpu - a_ora) / a_ora
+    assert np.quantile(err[agree], 0.999) < 1e-4 and np.max(err[agree]) < 1e-2
+    rel = np.abs(f_gpu - f_ora) / f_ora
+    assert np.quantile(rel[:, agree], 0.999) < 1e-4
+
+
+@pytest.mark.parametrize("D,dims", [(2, (77, 41, 1)), (3, (19, 17, 10))])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 1e-5)])
+def test_subgrid_viscosity(D, dims, storage, tol):
+    """nu_T = theta (2 - alpha) / (2 alpha beta), theta = 1/3 (Sec. VI, Eq. nuT), from the
+    oracle's path length of the same state; zero exactly on cutoff nodes."""
+    beta = 0.998
+    f0 = noisy_state(D, dims, 0.6e-3, seed=17, u0=0.002)  # |x|max straddles the 1e-3 cutoff
+    if storage == "f32":
+        f0 = f0.astype(np.float32)
+    f_pre = O.stream(D, dims, f0.astype(np.float64))
+    with E.Simulation(LAT[D], dims, beta, storage=storage, cutoff=True) as sim:
+        sim.set_populations(f0)
+        nut = sim.subgrid_viscosity().cpu().numpy()
+        _, fl = [t.cpu().numpy() for t in sim.alpha_field()]
+    a_ora, br_ora, _ = O.alpha_field(D, f_pre, beta, cutoff=True)
+    agree = check_branches(D, f_pre, fl, br_ora, 1e-12 if storage == "f64" else 1e-6)
+    want = (1.0 / 3.0) * (2.0 - a_ora) / (2.0 * a_ora * beta)
+    assert np.max(np.abs(nut - want)[agree]) < tol
+    assert np.all(nut[fl == E.ELBM_BRANCH_CUTOFF] == 0.0)
+    assert np.any(fl == E.ELBM_BRANCH_CUTOFF) and np.any(fl == E.ELBM_BRANCH_SOLVED)
 
 
 @pytest.mark.parametrize("D,L,nsteps", [(2, 96, 40), (3, 32, 20)])
