@@ -347,11 +347,10 @@ def run_gpu(args):
     peak, peak_src = measured_peaks()
     elem = {"f32": 4, "f16dev": 2, "bf16dev": 2}[args.storage]
     bytes_per_node = 2 * LATTICE_Q * elem
-    rows_ok = (L * elem) % 16 == 0 and L <= 512  # the ROWS kernel applies (see elbm.h)
-    kname = ("k_step_rows" if (args.kernel == "rows" or (args.kernel == "auto" and rows_ok))
-             else "k_step") + f"<{args.storage}> (D3Q27)"
+    # AUTO launches the DIRECT kernel (elbm.h)
+    kname = ("k_step_rows" if args.kernel == "rows" else "k_step") + f"<{args.storage}> (D3Q27)"
     achieved = bytes_per_node * N / kern_avg / 1e9
-    traffic = profiled_traffic() if (args.storage == STORAGE and args.kernel == "auto") else None
+    traffic = profiled_traffic() if (args.storage == STORAGE and args.kernel != "rows") else None
     value = aggregate_mlups(N, args.steps, world, elapsed)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -503,6 +502,65 @@ def run_precision(args):
     return 0
 
 
+def run_adjoint(args):
+    """Gradient of the final kinetic energy with respect to the initial velocity field:
+    D2Q9 256^2 periodic, beta = 0.9, u0 from the random-phase vortex generator (rms 0.02),
+    FP32, K steps (default 2000) with sqrt(K) checkpointing through the hand-written
+    adjoint.  Reports forward and forward+backward throughput and the agreement of
+    <dL/du0, v> with central differences (h = 1e-4) of the FP64 forward along seeded
+    directions v."""
+    import torch
+
+    from paper_2203_12946_gb300 import elbm as E
+    from paper_2203_12946_gb300 import inputs
+    from paper_2203_12946_gb300.adjoint import kinetic_energy_rollout
+
+    torch.cuda.set_device(0)
+    Ls, beta, T = args.adjoint_L, 0.9, args.steps
+    dims = (Ls, Ls, 1)
+    rho0, u0 = inputs.random_vortex_2d(Ls, rms=0.02, seed=inputs.DEFAULT_SEED)
+    with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f32", cutoff=False) as sim:
+        rt = torch.from_numpy(rho0).cuda()
+        # warm-up: a short rollout loads the kernels and fills the allocator's cache
+        uw = torch.from_numpy(u0).cuda().requires_grad_(True)
+        kinetic_energy_rollout(uw, sim, max(args.warmup, 3), rho0=rt).backward()
+        ut = torch.from_numpy(u0).cuda().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = kinetic_energy_rollout(ut, sim, T, rho0=rt)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        grad = ut.grad.cpu().numpy()
+    rng = np.random.default_rng(inputs.DEFAULT_SEED)
+    checks = []
+    h = 1e-4
+    for k in range(args.fd_dirs):
+        v = rng.standard_normal(u0.shape) * 0.01
+        Lpm = []
+        for sgn in (1, -1):
+            with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64", cutoff=False) as sim:
+                sim.init_equilibrium(rho0, u0 + sgn * h * v)
+                sim.step(T)
+                Lpm.append(sim.kinetic_energy())
+        fd = (Lpm[0] - Lpm[1]) / (2 * h)
+        ad = float(np.sum(grad * v))
+        checks.append({"fd": fd, "adjoint": ad, "rel_err": abs(ad - fd) / abs(fd)})
+    n = Ls * Ls * T
+    line = {
+        "metric": "adjoint rollout, D2Q9 256^2, dL/du0 of the final kinetic energy",
+        "config": {"workload": "adjoint", "dims": [Ls, Ls], "beta": beta, "steps": T, "storage": "f32",
+                   "checkpoint_every": int(np.ceil(np.sqrt(T))), "u0_rms": 0.02},
+        "loss": float(loss.detach()), "forward_mlups": n / (t1 - t0) / 1e6,
+        "backward_mlups": n / (t2 - t1) / 1e6,
+        "fd_checks": checks, "max_rel_err": max(c["rel_err"] for c in checks),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,12 +571,14 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "direct", "rows"], default="auto")
-    ap.add_argument("--workload", choices=["tgv3d", "ensemble", "precision"], default="tgv3d",
+    ap.add_argument("--workload", choices=["tgv3d", "ensemble", "precision", "adjoint"], default="tgv3d",
                     help="tgv3d: the benchmark (D3Q27 256^3); ensemble: batched D2Q9 domains; "
                          "precision: storage error study on the D2Q9 shear layer")
     ap.add_argument("--shear-L", type=int, default=1024)
     ap.add_argument("--checkpoints", default="1000,5000,20000")
     ap.add_argument("--oracle-steps", type=int, default=50)
+    ap.add_argument("--adjoint-L", type=int, default=256)
+    ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--storage", choices=["f32", "f16dev", "bf16dev"], default=STORAGE)
     ap.add_argument("--L", type=int, default=L, help="domain side (profiling runs only; "
                     "the benchmark workload is 256)")
@@ -533,6 +593,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_gpu(args)
 
 
