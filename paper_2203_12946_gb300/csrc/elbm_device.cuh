@@ -215,7 +215,9 @@ __device__ __forceinline__ T quad_root(T a, T b, T c)
 //    (2-s)(2u+s) = (1-u)(2s-1+3u) and 1/z(u) = z(-u)): one reciprocal per axis,
 //    and the first moment (eps(+1) - eps(-1))/6 = u carries no bias from it.
 //  * The Gauss-Legendre denominator factors: 60 + 90x + 36x^2 + 3x^3 =
-//    (2 + x)(30 + 30x + 3x^2), so the c1 and c terms share one reciprocal.
+//    (2 + x)(30 + 30x + 3x^2), so the c1 and c terms share one reciprocal,
+//    and as 60 + 60x + 11x^2 = 2(30 + 30x + 3x^2) + 5x^2, c = c1 + 5 <f, A x^2>
+//    with A = x^2 / ((2 + x)(30 + 30x + 3x^2)).
 //  * The Omega+ bracket 2/(4+t) + 1/(4+2t) + 2/(4+3t) is the single rational
 //    (80 + 80t + 19t^2) / (64 + 96t + 44t^2 + 6t^3).
 //  * a is assembled from the Omega- power sums S_k = <f, x^k>_- (k = 3..6);
@@ -329,7 +331,7 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
             const T A = div_(fx2, (T(2) + xi) * K);
             b1 += fx2;
             c1 += A * K;
-            c += A * (T(60) + xi * (T(60) + T(11) * xi));
+            c += A * (xi * xi); // c = c1 + 5 <f, A x^2> below
             if (xi < T(0)) {
                 const T fx3 = fx2 * xi;
                 S3 += fx3;
@@ -340,6 +342,7 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
         }
         b1 *= T(0.5);
         c1 *= T(2);
+        c = c1 + T(5) * c;
         if (b1 > T(0)) {
             // alpha_Lower (Eq. alphaLowerSoln).
             const T aL = quad_root(T(0.5) * S3, b1, c1);
@@ -516,11 +519,9 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         return A + el + A * el;
     };
 
-    // x_i = (f^eq_i - f_i) / f_i, and in the same pass the x-only sums of Eq. alphaLowerCoeffs / qaud_tight_coeff and the
-    // Omega- power sums (wasted only where the whole warp ends on the cutoff branch).
+    // x_i = (f^eq_i - f_i) / f_i and its extremes; the sums of the path length are
+    // taken only past the cutoff test, so warps whose nodes all take the shortcut skip them.
     float xabs = 0.0f, xmin = 0.0f;
-    float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f);
-    float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const float2 E = f2(E_of(2 * k), E_of(2 * k + 1));
@@ -532,25 +533,33 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         xp[k] = xi;
         xabs = fmaxf(xabs, fmaxf(fabsf(xi.x), fabsf(xi.y))); // three-input max
         xmin = fminf(xmin, fminf(xi.x, xi.y));
-        const float2 fx2 = pmul(delta, xi); // f x^2
-        const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
-        const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
-        b1 = padd(b1, fx2);
-        c1 = pfma(A, K, c1);
-        c = pfma(A, pfma(pfma(f2(11.0f), xi, f2(60.0f)), xi, f2(60.0f)), c);
-        const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
-        const float2 q = pmul(fx2, xm); // f x^3 on Omega-, 0 elsewhere
-        const float2 xm2 = pmul(xm, xm);
-        S3 = padd(S3, q);
-        S4 = pfma(q, xm, S4);
-        S5 = pfma(q, xm2, S5);
-        S6 = pfma(pmul(q, xm), xm2, S6);
     }
 
     float alpha = 2.0f;
     int br = kBranchCutoff;
     if (p.mode != kModeLBGK && !(p.cutoff && xabs < float(kCutoff))) {
-        const float sb1 = 0.5f * (b1.x + b1.y), sc1 = 2.0f * (c1.x + c1.y), sc = c.x + c.y;
+        // Eq. alphaLowerCoeffs and the x-only parts of Eq. qaud_tight_coeff, and the
+        // Omega- power sums S3..S6 (as in node_collide).
+        float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f);
+        float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 xi = xp[k];
+            const float2 fx2 = pmul(pmul(fp[k], xi), xi); // f x^2
+            const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
+            const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
+            b1 = padd(b1, fx2);
+            c1 = pfma(A, K, c1);
+            c = pfma(pmul(A, xi), xi, c); // c = c1 + 5 <f, A x^2> below
+            const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+            const float2 q = pmul(fx2, xm); // f x^3 on Omega-, 0 elsewhere
+            const float2 xm2 = pmul(xm, xm);
+            S3 = padd(S3, q);
+            S4 = pfma(q, xm, S4);
+            S5 = pfma(q, xm2, S5);
+            S6 = pfma(pmul(q, xm), xm2, S6);
+        }
+        const float sb1 = 0.5f * (b1.x + b1.y), sc1 = 2.0f * (c1.x + c1.y), sc = sc1 + 5.0f * (c.x + c.y);
         const float s3 = S3.x + S3.y, s4 = S4.x + S4.y, s5 = S5.x + S5.y, s6 = S6.x + S6.y;
         if (sb1 > 0.0f) {
             const float aL = quad_root(0.5f * s3, sb1, sc1); // alpha_Lower

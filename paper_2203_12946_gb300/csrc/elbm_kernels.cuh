@@ -23,7 +23,12 @@ namespace ELBM_SUFFIX {
 
 constexpr int D = ELBM_DIM;
 constexpr int Q = Lattice<D>::Q;
-constexpr int kStepBlock = D == 2 ? 256 : 128;
+// Threads per block of the direct step kernel (a tuning knob: block sizes that are
+// not a multiple of the register allocation unit leave resident warps unused).
+#ifndef ELBM_STEP_BLOCK_D3
+#define ELBM_STEP_BLOCK_D3 128
+#endif
+constexpr int kStepBlock = D == 2 ? 256 : ELBM_STEP_BLOCK_D3;
 constexpr int kAuxBlock = 256;
 
 __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x, int &y, int &z)
@@ -35,8 +40,8 @@ __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x
 }
 
 // One node per thread.  Launched either on a 3D grid (x from blockIdx.x,
-// y = blockIdx.y, z = blockIdx.z: no index arithmetic) or, when ny or nz exceed
-// the grid limits, on a 1D grid over all nodes.
+// y = blockIdx.y, z = blockIdx.z: no index arithmetic, 32-bit offsets) or, when
+// ny or nz exceed the grid limits or Q N reaches 2^32, on a 1D grid over all nodes.
 // Minimum resident blocks per SM requested from the register allocator for the
 // direct step kernel (0: let the compiler choose).
 #ifndef ELBM_STEP_MIN_BLOCKS
@@ -54,26 +59,43 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
                                                     CollideParams p)
 {
     using T = typename ST::T;
-    int x, y, z;
-    int64_t n;
-    if (kGrid3D) {
-        x = int(blockIdx.x) * kStepBlock + int(threadIdx.x);
-        if (x >= g.nx) return;
-        y = int(blockIdx.y);
-        z = int(blockIdx.z);
-        n = ((int64_t)z * g.ny + y) * g.nx + x;
-    } else {
-        n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
-        if (n >= g.N) return;
-        node_coords(n, g, x, y, z);
-    }
     T f[Q], xd[Q];
     const T rho0 = T(p.rho0);
-    pull_load<D, ST>(fin, g, x, y, z, rho0, f);
     int br;
-    collide<D, T, true>(f, xd, p, &br);
+    if constexpr (kGrid3D) {
+        // 3D grid with Q N < 2^32: element offsets in 32 bits (the source rows of
+        // (y - c_y, z - c_z) depend on the block only).  Measured faster on GB300 than
+        // per-thread base pointers with block-uniform row offsets.
+        const uint32_t x = blockIdx.x * kStepBlock + threadIdx.x;
+        const uint32_t nx = uint32_t(g.nx), ny = uint32_t(g.ny), nz = uint32_t(g.nz), N = uint32_t(g.N);
+        if (x >= nx) return;
+        const uint32_t y = blockIdx.y, z = blockIdx.z;
+        const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
+        for (int i = 0; i < Q; ++i) {
+            const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+            const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+            const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+            const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+            const uint32_t off = uint32_t(i) * N + (sz * ny + sy) * nx + sx;
+            f[i] = ST::load(__ldg(fin + off), T(weight(D, i)), rho0);
+        }
+        collide<D, T, true>(f, xd, p, &br);
+        const uint32_t n = (z * ny + y) * nx + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::store(f[i], T(weight(D, i)), rho0));
+    } else {
+        const int64_t n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
+        if (n >= g.N) return;
+        int x, y, z;
+        node_coords(n, g, x, y, z);
+        pull_load<D, ST>(fin, g, x, y, z, rho0, f);
+        collide<D, T, true>(f, xd, p, &br);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
+    }
 }
 
 // FP64 equilibrium from rho and u (same product form as node_collide).
@@ -572,7 +594,7 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
 #undef ELBM_ROWS_FOR
     }
     if (kernel == ELBM_KERNEL_ROWS) return cudaErrorNotSupported;
-    if (g.ny <= 65535 && g.nz <= 65535) {
+    if (g.ny <= 65535 && g.nz <= 65535 && uint64_t(Q) * uint64_t(g.N) <= 0xffffffffull) {
         const dim3 grid(unsigned((g.nx + kStepBlock - 1) / kStepBlock), unsigned(g.ny), unsigned(g.nz));
         ELBM_STORAGE_SWITCH(storage, (k_step<ST, true><<<grid, kStepBlock, 0, s>>>(
                                          static_cast<const typename ST::S *>(fin),

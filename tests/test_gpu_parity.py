@@ -430,6 +430,21 @@ def test_degenerate_domains(D, dims):
     assert np.max(np.abs(f_gpu - f_ora) / f_ora) < 1e-12
 
 
+@pytest.mark.parametrize("D,dims,storage", [(2, (3, 70001, 1), "f32"), (2, (2, 66000, 1), "f64"),
+                                            (3, (2, 2, 65537), "f32")])
+def test_one_dimensional_launch(D, dims, storage):
+    """ny or nz above the grid limit of a 3D launch: the kernel runs on a 1D grid with
+    64-bit node indices; same results as the oracle."""
+    beta = 0.99
+    f0 = noisy_state(D, dims, 3e-3, seed=41)
+    if storage == "f32":
+        f0 = f0.astype(np.float32)
+    f_gpu = gpu_run(D, dims, beta, f0, 2, storage, cutoff=False)
+    f_ora, *_ = O.step(D, dims, f0.astype(np.float64), beta, cutoff=False, nsteps=2)
+    tol = 1e-12 if storage == "f64" else 4e-6
+    assert np.max(np.abs(f_gpu - f_ora) / f_ora) < tol
+
+
 def test_zero_steps_and_uniform_fixed_point():
     D, dims = 3, (9, 8, 7)
     N = int(np.prod(dims))
