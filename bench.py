@@ -359,7 +359,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "lattice": "D3Q27", "dims": [L, L, L], "beta": BETA,
                    "u0": U0, "storage": args.storage, "diag_every": DIAG_EVERY,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (two 1.81 GB population buffers)"},
+                   "l2": "inputs larger than L2 (two %.2f GB population buffers)" % (LATTICE_Q * N * elem / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": kname,

@@ -33,6 +33,14 @@ constexpr int kAuxBlock = 256;
 
 __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x, int &y, int &z)
 {
+    if (g.N <= 0xffffffffll) { // 32-bit division where the indices fit (the common case)
+        const uint32_t m = uint32_t(n), nx = uint32_t(g.nx), ny = uint32_t(g.ny);
+        const uint32_t t = m / nx;
+        x = int(m - t * nx);
+        z = int(t / ny);
+        y = int(t - uint32_t(z) * ny);
+        return;
+    }
     const int64_t t = n / g.nx;
     x = int(n - t * g.nx);
     z = int(t / g.ny);
@@ -270,19 +278,54 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
             // H[f] = <f, log(f/w)> - rho (Eq. hdef), with log(f/w) = log1p(d/w), and
             // the entropy change of this node's collision (Eq. deltaH3, with <f,x> = 0
             // removing alpha beta <f,x> from both sums):
-            // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>.
+            // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>, g(y) = (1+y) log(1+y) - y.
             // Per-node sums in the path's compute type, domain sums in FP64.
             const T ab = alpha_t * T(p.beta);
-            T hl = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            T hl = T(0), s3 = T(0), xa = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const T fi = fc[i], xi = xd[i];
                 hl += fi * log1p((fi - T(weight(D, i))) * T(1.0 / weight(D, i)));
-                s1 += fi * g_entropy<T>(ab * xi);
-                s2 += fi * xi * log1p(xi);
                 s3 += fi * xi * xi;
+                xa = fmax(xa, fabs(xi));
             }
-            const double dH = double(s1) - double(ab) * double(s2);
+            double dH;
+            if (xa < T(0.1) && ab <= T(2.2)) {
+                // g(ab x) - ab x log(1+x) = sum_{k>=2} c_k x^k,
+                // c_k = (-1)^k ab/(k-1) (ab^(k-1)/k - 1), summed to k = kTop (for |x| < 0.1
+                // and ab <= 2.2 the rest is below 5e-10 x^2).  c_2 = ab (ab - 2)/2 takes
+                // ab - 2 from one rounding of alpha beta - 2; the two sums of the direct
+                // form cancel to that small leading coefficient instead.
+                constexpr int kTop = 13;
+                T ck[kTop + 1];
+                ck[2] = T(0.5) * ab * fma(alpha_t, T(p.beta), T(-2));
+                T abk = ab * ab; // ab^(k-1) at k = 3
+#pragma unroll
+                for (int k = 3; k <= kTop; ++k) {
+                    const T v = ab / T(k - 1) * (abk / T(k) - T(1));
+                    ck[k] = (k & 1) ? -v : v;
+                    abk *= ab;
+                }
+                T sd = T(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const T xi = xd[i];
+                    T poly = ck[kTop];
+#pragma unroll
+                    for (int k = kTop - 1; k >= 2; --k) poly = fma(poly, xi, ck[k]);
+                    sd += fc[i] * (poly * xi * xi);
+                }
+                dH = double(sd);
+            } else {
+                T s1 = T(0), s2 = T(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const T fi = fc[i], xi = xd[i];
+                    s1 += fi * g_entropy<T>(ab * xi);
+                    s2 += fi * xi * log1p(xi);
+                }
+                dH = double(s1) - double(ab) * double(s2);
+            }
             sum[4] += double(hl) - (1.0 + weight_sum_error<D, T>() + double(dr));
             dmax = max(dmax, ordered_bits(dH));
             if (dH > 1e-6 * double(s3) && s3 > T(0)) cnt[4] += 1;
