@@ -112,10 +112,15 @@ def _load():
             "or_H_total": (ctypes.c_double, [ctypes.c_int, _i64, _D]),
             "or_max_threads": (ctypes.c_int, []),
             "or_collide_vjp": (None, [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_int, ctypes.c_double, _D]),
+                                      ctypes.c_int, _D, ctypes.c_double, _D]),
             "or_step_adjoint": (None, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_double, ctypes.c_int,
-                                       ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
                                        ctypes.c_int]),
+            "or_force_node": (None, [ctypes.c_int, _D, _D]),
+            "or_force": (None, [ctypes.c_int, _i64, _D, _D, ctypes.c_int]),
+            "or_step_force_vjp": (None, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_double, _D,
+                                         ctypes.c_int]),
             "or_kinetic_energy": (ctypes.c_double, [ctypes.c_int, _i64, _D, _D]),
         }
         for name, (res, args) in sig.items():
@@ -309,14 +314,29 @@ def alpha_field(D: int, f, beta: float, cutoff: bool = True, b_variant: int = B_
     return a, br, ae
 
 
+def _force3(D, force):
+    F = np.zeros(3)
+    F[:D] = np.asarray(force, dtype=np.float64).ravel()[:D]
+    return F
+
+
+def force_node(D: int, f, force) -> np.ndarray:
+    """One node's populations after the exact-difference body-force term (not in the paper)."""
+    f = _f64(f).copy()
+    _load().or_force_node(D, _dp(_force3(D, force)), _dp(f))
+    return f
+
+
 def step(D: int, dims, f, beta: float, cutoff: bool = True, b_variant: int = B_DERIVED,
          mode: int = MODE_HIGHER, nsteps: int = 1, nthreads: int = 0, want_alpha: bool = False,
-         want_dH: bool = False):
-    """Advance a post-collision field by ``nsteps`` steps (stream, then collide).
+         want_dH: bool = False, force=None):
+    """Advance a post-collision field by ``nsteps`` steps (stream, then collide, then the
+    body-force term when ``force`` is given).
 
     Returns (f, alpha, branch, dH) where the optional per-node fields belong to
     the last step.
     """
+    F = None if force is None else _force3(D, force)
     nx, ny, nz = _dims(D, dims)
     a = _f64(f).copy()
     b = np.zeros_like(a)
@@ -331,6 +351,8 @@ def step(D: int, dims, f, beta: float, cutoff: bool = True, b_variant: int = B_D
         lib.or_step(D, nx, ny, nz, float(beta), int(bool(cutoff)), int(b_variant), int(mode),
                     _dp(a), _dp(b), _dp(alpha_), None if br is None else br.ctypes.data_as(_I8),
                     _dp(dh), int(nthreads))
+        if F is not None:
+            lib.or_force(D, N, _dp(F), _dp(b), int(nthreads))
         a, b = b, a
     return a, alpha_, br, dh
 
@@ -340,24 +362,39 @@ def step(D: int, dims, f, beta: float, cutoff: bool = True, b_variant: int = B_D
 # ----------------------------------------------------------------------------
 
 def collide_vjp(D: int, f, g, beta: float, cutoff: bool = False, b_variant: int = B_DERIVED,
-                mode: int = MODE_HIGHER, eps: float = 1e-5) -> np.ndarray:
+                mode: int = MODE_HIGHER, eps: float = 1e-5, force=None) -> np.ndarray:
     """h = J^T g of one node's collision (J = d f* / d f), by central differences."""
     f, g = _f64(f), _f64(g)
     h = np.zeros_like(f)
+    F = None if force is None else _force3(D, force)
     _load().or_collide_vjp(D, _dp(f), _dp(g), float(beta), int(bool(cutoff)), int(b_variant), int(mode),
-                           float(eps), _dp(h))
+                           _dp(F), float(eps), _dp(h))
     return h
 
 
 def step_adjoint(D: int, dims, f_t, g_next, beta: float, cutoff: bool = False, b_variant: int = B_DERIVED,
-                 mode: int = MODE_HIGHER, eps: float = 1e-5, nthreads: int = 0) -> np.ndarray:
-    """dL/df^t from dL/df^{t+1} for f^{t+1} = collide(stream(f^t))."""
+                 mode: int = MODE_HIGHER, eps: float = 1e-5, nthreads: int = 0, force=None) -> np.ndarray:
+    """dL/df^t from dL/df^{t+1} for f^{t+1} = collide(stream(f^t)) (+ the force term)."""
     nx, ny, nz = _dims(D, dims)
     f_t, g_next = _f64(f_t), _f64(g_next)
     g_t = np.zeros_like(f_t)
+    F = None if force is None else _force3(D, force)
     _load().or_step_adjoint(D, nx, ny, nz, float(beta), int(bool(cutoff)), int(b_variant), int(mode),
-                            _dp(f_t), _dp(g_next), _dp(g_t), float(eps), int(nthreads))
+                            _dp(F), _dp(f_t), _dp(g_next), _dp(g_t), float(eps), int(nthreads))
     return g_t
+
+
+def step_force_vjp(D: int, dims, f_t, g_next, beta: float, force, cutoff: bool = False,
+                   b_variant: int = B_DERIVED, mode: int = MODE_HIGHER, eps: float = 1e-6,
+                   nthreads: int = 0) -> np.ndarray:
+    """d/dF of <g_next, f^{t+1}> for one forced step (D values), by central differences."""
+    nx, ny, nz = _dims(D, dims)
+    f_t, g_next = _f64(f_t), _f64(g_next)
+    out = np.zeros(3)
+    _load().or_step_force_vjp(D, nx, ny, nz, float(beta), int(bool(cutoff)), int(b_variant), int(mode),
+                              _dp(_force3(D, force)), _dp(f_t), _dp(g_next), float(eps), _dp(out),
+                              int(nthreads))
+    return out[:D]
 
 
 def kinetic_energy(D: int, f, want_grad: bool = True):

@@ -14,6 +14,11 @@
  * algorithm (Appendix D).  All arithmetic is IEEE double; nothing is fused or
  * reordered beyond what the formulas say.
  *
+ * Two parts have no passage in the paper and say so where they are defined:
+ * the uniform body force (an exact-difference term added after the collision)
+ * and the adjoint of the step (node Jacobians by central differences), both
+ * used to check gradients.
+ *
  * Readings where the paper is ambiguous (each also listed in the design doc):
  *  R1  the product-form equilibrium carries one factor Upsilon_a per axis
  *      (Sec. I, D2Q9/D3Q27 equilibrium), and with theta0 = 1/3 the exponent
@@ -511,6 +516,39 @@ void or_alpha_field(int D, int64_t N, double beta, int cutoff, int b_variant, in
 
 /* One time step: stream (Eq. advection) then collide (Eq. fstar_def).      */
 /* The stored state is post-collision; fin and fout must not alias.         */
+/* Uniform body force (the paper has none; used by the gradient workload).      */
+/* Exact-difference forcing applied after the collision:                       */
+/*   f_i += f^eq_i(rho, u + F/rho) - f^eq_i(rho, u),                           */
+/* rho, u the node's moments (which the collision conserves).  Mass is          */
+/* unchanged and the momentum grows by exactly F per step.                      */
+void or_force_node(int D, const double *force, double *f)
+{
+    double rho, u[3], v[3], feq0[OR_QMAX], feq1[OR_QMAX];
+    int Q = 1, a, i;
+    for (a = 0; a < D; a++) Q *= 3;
+    or_moments(D, f, &rho, u);
+    for (a = 0; a < D; a++) v[a] = u[a] + force[a] / rho;
+    or_equilibrium(D, rho, u, feq0);
+    or_equilibrium(D, rho, v, feq1);
+    for (i = 0; i < Q; i++) f[i] += feq1[i] - feq0[i];
+}
+
+void or_force(int D, int64_t N, const double *force, double *f, int nthreads)
+{
+    int Q = 1, a;
+    int64_t n;
+    for (a = 0; a < D; a++) Q *= 3;
+    or_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (n = 0; n < N; n++) {
+        double fn[OR_QMAX];
+        int i;
+        for (i = 0; i < Q; i++) fn[i] = f[(int64_t)i * N + n];
+        or_force_node(D, force, fn);
+        for (i = 0; i < Q; i++) f[(int64_t)i * N + n] = fn[i];
+    }
+}
+
 void or_step(int D, int64_t nx, int64_t ny, int64_t nz, double beta, int cutoff, int b_variant,
              int mode, const double *fin, double *fout, double *alpha_out, int8_t *branch_out,
              double *dH_out, int nthreads)
@@ -590,7 +628,7 @@ int or_max_threads(void)
 
 /* One node: f (pre-collision, Q values) -> f* (Eq. fstar_def with alpha). */
 static void or_collide_node(int D, const double *f, double beta, int cutoff, int b_variant, int mode,
-                            double *fs)
+                            const double *force, double *fs)
 {
     double feq[OR_QMAX], rho, u[3];
     or_alpha_info info;
@@ -600,11 +638,12 @@ static void or_collide_node(int D, const double *f, double beta, int cutoff, int
     or_equilibrium(D, rho, u, feq);
     or_alpha(Q, f, feq, beta, cutoff, b_variant, mode, &info);
     or_relax(Q, f, feq, info.alpha, beta, fs);
+    if (force) or_force_node(D, force, fs);
 }
 
 /* h_j = sum_i g_i d f*_i / d f_j at one node, by central differences. */
 void or_collide_vjp(int D, const double *f, const double *g, double beta, int cutoff, int b_variant, int mode,
-                    double eps, double *h)
+                    const double *force, double eps, double *h)
 {
     double fp[OR_QMAX], fm[OR_QMAX], sp[OR_QMAX], sm[OR_QMAX];
     int Q = 1, a, i, j;
@@ -615,8 +654,8 @@ void or_collide_vjp(int D, const double *f, const double *g, double beta, int cu
         memcpy(fm, f, sizeof(double) * Q);
         fp[j] += d;
         fm[j] -= d;
-        or_collide_node(D, fp, beta, cutoff, b_variant, mode, sp);
-        or_collide_node(D, fm, beta, cutoff, b_variant, mode, sm);
+        or_collide_node(D, fp, beta, cutoff, b_variant, mode, force, sp);
+        or_collide_node(D, fm, beta, cutoff, b_variant, mode, force, sm);
         for (i = 0; i < Q; i++) acc += g[i] * (sp[i] - sm[i]);
         h[j] = acc / (2.0 * d);
     }
@@ -624,7 +663,8 @@ void or_collide_vjp(int D, const double *f, const double *g, double beta, int cu
 
 /* dL/df^t from dL/df^{t+1}, where f^{t+1} = collide(stream(f^t)) (fields SoA). */
 void or_step_adjoint(int D, int64_t nx, int64_t ny, int64_t nz, double beta, int cutoff, int b_variant, int mode,
-                     const double *f_t, const double *g_next, double *g_t, double eps, int nthreads)
+                     const double *force, const double *f_t, const double *g_next, double *g_t, double eps,
+                     int nthreads)
 {
     int c[OR_QMAX * 3];
     double w[OR_QMAX];
@@ -646,7 +686,7 @@ void or_step_adjoint(int D, int64_t nx, int64_t ny, int64_t nz, double beta, int
                     fn[i] = F[(int64_t)i * N + n];
                     gn[i] = g_next[(int64_t)i * N + n];
                 }
-                or_collide_vjp(D, fn, gn, beta, cutoff, b_variant, mode, eps, h);
+                or_collide_vjp(D, fn, gn, beta, cutoff, b_variant, mode, force, eps, h);
                 /* F_i(x) = f^t_i(x - c_i): the adjoint sends h_i(x) back to x - c_i */
                 for (i = 0; i < Q; i++) {
                     int64_t sx = or_wrap(xx - c[i * D + 0], nx);
@@ -661,6 +701,39 @@ void or_step_adjoint(int D, int64_t nx, int64_t ny, int64_t nz, double beta, int
 
 /* Kinetic energy L = 1/2 sum_x rho |u|^2 of a field and its gradient          */
 /* dL/df_i = c_i . u - |u|^2 / 2 at every node.                               */
+/* d/dF of sum_x <g_next(x), f^{t+1}(x)> for one forced step, by central        */
+/* differences in each force component (dF_out: D values).                     */
+void or_step_force_vjp(int D, int64_t nx, int64_t ny, int64_t nz, double beta, int cutoff, int b_variant,
+                       int mode, const double *force, const double *f_t, const double *g_next, double eps,
+                       double *dF_out, int nthreads)
+{
+    int Q = 1, a, b;
+    int64_t N = nx * ny * nz, n;
+    double *F;
+    for (a = 0; a < D; a++) Q *= 3;
+    F = (double *)malloc(sizeof(double) * (size_t)Q * (size_t)N);
+    if (!F) return;
+    or_stream(D, nx, ny, nz, f_t, F, nthreads);
+    for (b = 0; b < D; b++) {
+        double acc = 0.0;
+        or_set_threads(nthreads);
+#pragma omp parallel for schedule(static) reduction(+ : acc)
+        for (n = 0; n < N; n++) {
+            double fn[OR_QMAX], sp[OR_QMAX], sm[OR_QMAX], fp_[3], fm_[3];
+            int i, k;
+            for (i = 0; i < Q; i++) fn[i] = F[(int64_t)i * N + n];
+            for (k = 0; k < 3; k++) fp_[k] = fm_[k] = (k < D) ? force[k] : 0.0;
+            fp_[b] += eps;
+            fm_[b] -= eps;
+            or_collide_node(D, fn, beta, cutoff, b_variant, mode, fp_, sp);
+            or_collide_node(D, fn, beta, cutoff, b_variant, mode, fm_, sm);
+            for (i = 0; i < Q; i++) acc += g_next[(int64_t)i * N + n] * (sp[i] - sm[i]) / (2.0 * eps);
+        }
+        dF_out[b] = acc;
+    }
+    free(F);
+}
+
 double or_kinetic_energy(int D, int64_t N, const double *f, double *grad)
 {
     int c[OR_QMAX * 3];

@@ -82,3 +82,65 @@ def test_kinetic_energy_gradient():
     Lp, _ = O.kinetic_energy(D, f + h * v, want_grad=False)
     Lm, _ = O.kinetic_energy(D, f - h * v, want_grad=False)
     assert abs((Lp - Lm) / (2 * h) - np.sum(g * v)) < 1e-8 * np.linalg.norm(g) * np.linalg.norm(v)
+
+
+# ---------------------------------------------------------------------------
+# Body force (exact-difference term after the collision; not in the paper)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_force_term_moments(D):
+    """The term f^eq(rho, u + F/rho) - f^eq(rho, u) leaves the mass and adds exactly F to the
+    momentum (both equilibria carry their moments exactly); F = 0 changes nothing."""
+    rng = np.random.default_rng(31 + D)
+    c, _ = O.lattice(D)
+    for _ in range(30):
+        f = state(rng, D, 10 ** rng.uniform(-3, -1))
+        F = rng.uniform(-1e-3, 1e-3, D)
+        g = O.force_node(D, f, F)
+        r0, u0 = O.moments(D, f)
+        r1, u1 = O.moments(D, g)
+        assert abs(r1 - r0) < 1e-15
+        assert np.max(np.abs(r1 * u1 - (r0 * u0 + F))) < 1e-15
+        assert np.array_equal(O.force_node(D, f, np.zeros(D)), f)
+
+
+@pytest.mark.parametrize("D,dims", [(2, (6, 5, 1)), (3, (4, 3, 3))])
+def test_uniform_flow_accelerates_linearly(D, dims):
+    """A uniform equilibrium stays an equilibrium under the forced step (x = 0, so alpha = 2
+    relaxes nothing), and u grows by F/rho per step: u(t) = u0 + t F / rho."""
+    N = int(np.prod(dims))
+    rho = np.full(N, 1.02)
+    u0 = np.array([0.01, -0.02, 0.015])[:D]
+    F = np.array([2e-4, 1e-4, -3e-4])[:D]
+    f = O.init_equilibrium(D, rho, np.repeat(u0[:, None], N, axis=1))
+    for t in (1, 7, 25):
+        ft, *_ = O.step(D, dims, f, 0.95, nsteps=t, force=F)
+        r, u = O.moments_field(D, ft)
+        assert np.max(np.abs(r - 1.02)) < 1e-13
+        assert np.max(np.abs(u - (u0 + t * F / 1.02)[:, None])) < 1e-13
+
+
+@pytest.mark.parametrize("D,dims", [(2, (7, 6, 1)), (3, (4, 4, 3))])
+def test_forced_step_adjoint_transpose_identity(D, dims):
+    """<g, d step / d f . v> against an independent directional difference of the forced
+    step, and d<g, step>/dF against differences in F."""
+    rng = np.random.default_rng(53 + D)
+    N = int(np.prod(dims))
+    f = np.stack([state(rng, D, 0.02) for _ in range(N)], axis=1)
+    F = rng.uniform(-5e-4, 5e-4, D)
+    g = rng.standard_normal(f.shape)
+    v = rng.standard_normal(f.shape) * f
+    h = 1e-6
+    fp, *_ = O.step(D, dims, f + h * v, 0.97, cutoff=False, force=F)
+    fm, *_ = O.step(D, dims, f - h * v, 0.97, cutoff=False, force=F)
+    lhs = np.sum(g * (fp - fm)) / (2 * h)
+    rhs = np.sum(O.step_adjoint(D, dims, f, g, 0.97, force=F) * v)
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+    dF = O.step_force_vjp(D, dims, f, g, 0.97, F)
+    for a in range(D):
+        e = np.zeros(D)
+        e[a] = 1e-5
+        sp, *_ = O.step(D, dims, f, 0.97, cutoff=False, force=F + e)
+        sm, *_ = O.step(D, dims, f, 0.97, cutoff=False, force=F - e)
+        assert abs(np.sum(g * (sp - sm)) / 2e-5 - dF[a]) <= 1e-6 * np.abs(dF).max()

@@ -19,6 +19,7 @@ SRC = os.path.join(ROOT, "oracle", "elbm_oracle.c")
 
 P = "tests/test_oracle_pins.py"
 F = "tests/test_oracle_field.py"
+A = "tests/test_oracle_adjoint.py"
 
 # name: (original text, planted text, pins expected to catch it)
 MUTANTS = {
@@ -70,6 +71,13 @@ MUTANTS = {
                       [P + "::test_d1q2_mirror_root_is_two"]),
     "moments_velocity_index": ("m[a] += f[i] * c[i * D + a];", "m[a] += f[i] * c[i * D + (D - 1 - a)];",
                                [P + "::test_equilibrium_has_the_prescribed_moments"]),
+    "force_not_divided_by_rho": ("v[a] = u[a] + force[a] / rho;", "v[a] = u[a] + force[a];",
+                                 [A + "::test_force_term_moments"]),
+    "force_sign": ("f[i] += feq1[i] - feq0[i];", "f[i] += feq0[i] - feq1[i];",
+                   [A + "::test_uniform_flow_accelerates_linearly"]),
+    "adjoint_push_direction": ("g_t[(int64_t)i * N + (sz * ny + sy) * nx + sx] = h[i];",
+                               "g_t[(int64_t)i * N + n] = h[i];",
+                               [A + "::test_step_adjoint_transpose_identity"]),
 }
 
 
