@@ -250,6 +250,24 @@ int elbm_set_populations(elbm_t *h, const void *src, int where);
  * pass takes; Omega+/- membership held fixed).  g_t must not alias g_next. */
 int elbm_adjoint_step(elbm_t *h, const void *f_t, const void *g_next, void *g_t);
 
+/* As elbm_adjoint_step, and also adds to dforce[0..D-1] (DEVICE pointer, FP64,
+ * accumulated, not overwritten) the derivative of sum_x <g_next(x), f^{t+1}(x)>
+ * with respect to the uniform body force of elbm_set_force, taken at the force
+ * currently set (zero included).  Summing over the steps of a reverse sweep
+ * gives dL/dF.  The paper defines no force and no adjoint; see elbm_set_force.
+ * Errors: ELBM_ERR_ARG (null pointer, g_t == g_next), ELBM_ERR_CUDA. */
+int elbm_adjoint_step_force(elbm_t *h, const void *f_t, const void *g_next, void *g_t, double *dforce);
+
+/* Uniform body force F (D host doubles; NULL = none), applied by every later
+ * elbm_step after the collision as the exact-difference term
+ *   f_i += f^eq_i(rho, u + F/rho) - f^eq_i(rho, u),
+ * rho, u the node's moments.  Not from the paper (which has no forcing): it
+ * serves gradient studies such as dL/dF.  It keeps the mass and adds exactly F
+ * to the momentum of every node per step.  A nonzero force uses the DIRECT
+ * kernel.  Errors: ELBM_ERR_ARG (non-finite component), ELBM_ERR_UNSUPPORTED
+ * (opts.kernel == ELBM_KERNEL_ROWS). */
+int elbm_set_force(elbm_t *h, const double *force);
+
 /* L = 1/2 sum_x rho |u|^2 of the field f (storage type, device; NULL = the
  * current state), accumulated in FP64 into *L (host; synchronises), and, if
  * grad is not NULL, dL/df_i = c_i . u - |u|^2/2 (compute type, device). */

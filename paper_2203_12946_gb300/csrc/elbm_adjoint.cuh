@@ -35,9 +35,12 @@ __device__ __forceinline__ RootGrad<T> root_grad(T a, T b, T c)
 }
 
 // h = J^T g for the collision at one node (pre-collision populations F).
-template <int D, class T>
-__device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin)[Lattice<D>::Q], const CollideParams &p,
-                         T (&h)[Lattice<D>::Q])
+// With kForce the node map is C(F) + Phi(C(F)), Phi the body-force term of
+// add_force (f^eq(rho, u + F_b/rho) - f^eq(rho, u)); the incoming adjoint passes
+// through Phi first, and dforce[a] receives this node's d<g, C + Phi>/dF_b,a.
+template <int D, class T, bool kForce = false>
+__device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin0)[Lattice<D>::Q], const CollideParams &p,
+                         T (&h)[Lattice<D>::Q], T *dforce = nullptr)
 {
     constexpr int Q = Lattice<D>::Q;
     const T beta = T(p.beta);
@@ -81,16 +84,17 @@ __device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin)[Lattice<D>:
         deps[a][2] = T(2) * v + T(3);
     }
     // E without axis `skip` (skip = D: all axes): prod (1 + eps) - 1, never rounding 1 + eps
-    auto E_excl = [&](int i, int skip) -> T {
+    auto E_excl_at = [&](const T (&ep)[D][3], int i, int skip) -> T {
         T e = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a)
             if (a != skip) {
-                const T ea = eps[a][vel(D, i, a) + 1];
+                const T ea = ep[a][vel(D, i, a) + 1];
                 e = e + ea + e * ea;
             }
         return e;
     };
+    auto E_excl = [&](int i, int skip) -> T { return E_excl_at(eps, i, skip); };
     T feq[Q], x[Q], delta[Q];
     T xabs = T(0), xmin = T(0);
     int imin = 0;
@@ -238,28 +242,30 @@ __device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin)[Lattice<D>:
         Fb[i] += -xb[i] * feq[i] / (F[i] * F[i]);
         lam[i] = xb[i] / F[i];
     }
-    // VJP of f^eq = rho W k_i prod_a (1 + eps_a(c_ia)), u = j / rho:
-    //   sum_i l_i d feq_i / d F_j = G_rho + sum_a G_a (c_ja - u_a) / rho,
+    // VJP of f^eq = rho W k_i prod_a (1 + eps_a(c_ia; v)) at a velocity v = (j + F_b)/rho
+    // (F_b = 0: v = u):
+    //   sum_i l_i d feq_i / d F_j = G_rho + sum_a G_a (c_ja - v_a) / rho,
     //   G_rho = sum_i l_i feq_i / rho,
     //   G_a = sum_i l_i (k_i r) eps_a'(c_ia) prod_{b != a} (1 + eps_b(c_ib)).
-    auto feq_vjp = [&](const T (&l)[Q], T (&out)[Q]) {
-        T Gr = T(0), Ga[D];
+    auto feq_vjp_at = [&](const T (&l)[Q], T (&out)[Q], const T (&ep)[D][3], const T (&dep)[D][3],
+                          const T (&vv)[D], const T (&fq)[Q], T (&Ga)[D]) {
+        T Gr = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) Ga[a] = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            Gr += l[i] * feq[i];
+            Gr += l[i] * fq[i];
             const T lk = l[i] * (T(weight_k(D, i)) * rW);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                const T q = lk * deps[a][vel(D, i, a) + 1];
-                Ga[a] += fma(q, E_excl(i, a), q);
+                const T q = lk * dep[a][vel(D, i, a) + 1];
+                Ga[a] += fma(q, E_excl_at(ep, i, a), q);
             }
         }
         Gr *= irho;
         T base = Gr;
 #pragma unroll
-        for (int a = 0; a < D; ++a) base -= Ga[a] * u[a] * irho;
+        for (int a = 0; a < D; ++a) base -= Ga[a] * vv[a] * irho;
 #pragma unroll
         for (int jj = 0; jj < Q; ++jj) {
             T v = base;
@@ -268,10 +274,48 @@ __device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin)[Lattice<D>:
             out[jj] = v;
         }
     };
+    auto feq_vjp = [&](const T (&l)[Q], T (&out)[Q]) {
+        T Ga[D];
+        feq_vjp_at(l, out, eps, deps, u, feq, Ga);
+    };
     T V[Q];
     feq_vjp(lam, V);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Fb[i] += V[i]; // Fb = d alpha / d F
+
+    // ---- the body-force term: gin = (I + dPhi/df*)^T gin0, and d/dF_b ----
+    T gin[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) gin[i] = gin0[i];
+    if constexpr (kForce) {
+        T v[D], epv[D][3], depv[D][3], feqv[Q], Gv[D], Gu[D], Vv[Q], Vu[Q];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            v[a] = u[a] + T(p.force[a]) * irho;
+            const T sq = sqrt(T(1) + T(3) * v[a] * v[a]);
+            const T t = T(3) * v[a] * v[a] / (T(1) + sq);
+            epv[a][0] = T(2) * t - T(3) * v[a];
+            epv[a][1] = -t;
+            epv[a][2] = T(2) * t + T(3) * v[a];
+            const T dv = T(3) * v[a] / sq;
+            depv[a][0] = T(2) * dv - T(3);
+            depv[a][1] = -dv;
+            depv[a][2] = T(2) * dv + T(3);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const T kr = T(weight_k(D, i)) * rW;
+            feqv[i] = fma(kr, E_excl_at(epv, i, D), kr);
+        }
+        feq_vjp_at(gin0, Vv, epv, depv, v, feqv, Gv);
+        feq_vjp_at(gin0, Vu, eps, deps, u, feq, Gu);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) gin[i] += Vv[i] - Vu[i];
+        if (dforce) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) dforce[a] += Gv[a] * irho; // d v_a / d F_b,a = 1/rho
+        }
+    }
 
     // ---- the collision's VJP: h_j = g_j + beta (s dalpha/dF_j + alpha (feq_vjp(g)_j - g_j)) ----
     T s = T(0);

@@ -3,6 +3,7 @@
 // step lives in the kernels (elbm_kernels.cuh); this file only marshals.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +34,7 @@ struct elbm {
     int *err_word = nullptr; // device: ELBM_ERR_TIMEOUT when a bounded device wait expired
     int num_sms = 0;
     int64_t steps = 0;
+    double force[3] = {0.0, 0.0, 0.0}; // uniform body force (elbm_set_force)
     std::string err;
 };
 
@@ -76,6 +78,7 @@ CollideParams params_of(const elbm_t *h)
     p.cutoff = h->opts.cutoff;
     p.b_variant = h->opts.b_variant;
     p.rho0 = h->opts.rho0;
+    for (int a = 0; a < 3; ++a) p.force[a] = h->force[a];
     return p;
 }
 
@@ -561,8 +564,35 @@ int elbm_adjoint_step(elbm_t *h, const void *f_t, const void *g_next, void *g_t)
     if (g_next == g_t) return fail(h, ELBM_ERR_ARG, "elbm_adjoint_step: g_t must not alias g_next");
     DeviceGuard guard(h->opts.device);
     cudaError_t e = ELBM_BY_LATTICE(h, launch_step_adjoint, h->opts.storage, f_t, g_next, g_t, h->g, params_of(h),
-                                    h->stream);
+                                    nullptr, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "elbm_adjoint_step: kernel launch");
+    return ELBM_OK;
+}
+
+int elbm_adjoint_step_force(elbm_t *h, const void *f_t, const void *g_next, void *g_t, double *dforce)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_adjoint_step_force: handle is NULL");
+    if (!f_t || !g_next || !g_t || !dforce) return fail(h, ELBM_ERR_ARG, "elbm_adjoint_step_force: null pointer");
+    if (g_next == g_t) return fail(h, ELBM_ERR_ARG, "elbm_adjoint_step_force: g_t must not alias g_next");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_step_adjoint, h->opts.storage, f_t, g_next, g_t, h->g, params_of(h),
+                                    dforce, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_adjoint_step_force: kernel launch");
+    return ELBM_OK;
+}
+
+int elbm_set_force(elbm_t *h, const double *force)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_set_force: handle is NULL");
+    double F[3] = {0.0, 0.0, 0.0};
+    if (force)
+        for (int a = 0; a < h->D; ++a) {
+            if (!std::isfinite(force[a])) return fail(h, ELBM_ERR_ARG, "elbm_set_force: component %d is not finite", a);
+            F[a] = force[a];
+        }
+    if (h->opts.kernel == ELBM_KERNEL_ROWS && (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0))
+        return fail(h, ELBM_ERR_UNSUPPORTED, "elbm_set_force: the body force runs on the DIRECT kernel only");
+    for (int a = 0; a < 3; ++a) h->force[a] = F[a];
     return ELBM_OK;
 }
 

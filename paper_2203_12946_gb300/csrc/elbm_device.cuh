@@ -82,6 +82,7 @@ struct CollideParams {
     int cutoff;    // 1 = Appendix D shortcut on
     int b_variant; // 0 = derived denominators (alpha_L beta x), 1 = printed (alpha_L x)
     double rho0;   // reference density of deviation storage
+    double force[3] = {0.0, 0.0, 0.0}; // uniform body force (not from the paper), used by the forced kernels
 };
 
 // ---------------------------------------------------------------------------
@@ -657,6 +658,72 @@ __device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin
         const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
         const int64_t src = ((int64_t)sz * g.ny + sy) * g.nx + sx;
         f[i] = ST::load(__ldg(fin + (int64_t)i * g.N + src), T(weight(D, i)), rho0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Uniform body force F (the paper has none; it serves gradient studies): after
+// the collision, the exact-difference term
+//   f_i += f^eq_i(rho, u + F/rho) - f^eq_i(rho, u)
+// with rho, u the node's moments (the collision conserves them).  It keeps the
+// mass and adds exactly F to the momentum.  Evaluated without rounding at the
+// scale of w_i u: per axis the factor difference
+//   eps(c; v) - eps(c; u) = 2 (t_v - t_u) + 3 c (v - u),
+//   t_v - t_u = s_v - s_u = 3 (v - u)(v + u) / (s_v + s_u),
+// and f^eq(v) - f^eq(u) = k_i r sum_a d_a prod_{b<a} (1 + eps_b(v)) prod_{b>a} (1 + eps_b(u))
+// with the products kept as 1 + (small).
+// ---------------------------------------------------------------------------
+template <int D, class T>
+__device__ __forceinline__ void add_force(T (&f)[Lattice<D>::Q], const CollideParams &p)
+{
+    constexpr int Q = Lattice<D>::Q;
+    T drho = T(0), j[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) j[a] = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T di = f[i] - T(weight_k(D, i)) * T(weight_unit(D)); // exact
+        drho += di;
+#pragma unroll
+        for (int a = 0; a < D; ++a) j[a] += T(vel(D, i, a)) * di;
+    }
+    drho -= T(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, T>()));
+    const T rho = T(1) + drho;
+    const T irho = T(1) / rho;
+    const T r = fma(rho, T(weight_unit(D)), rho * weight_unit_lo<D, T>());
+    T eu[D][3], ev[D][3], de[D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const T u = j[a] * irho, dv = T(p.force[a]) * irho, v = u + dv;
+        const T su = sqrt(T(1) + T(3) * u * u), sv = sqrt(T(1) + T(3) * v * v);
+        const T tu = T(3) * u * u / (T(1) + su), tv = T(3) * v * v / (T(1) + sv);
+        const T dt = T(3) * dv * (u + v) / (su + sv);
+        eu[a][0] = T(2) * tu - T(3) * u;
+        eu[a][1] = -tu;
+        eu[a][2] = T(2) * tu + T(3) * u;
+        ev[a][0] = T(2) * tv - T(3) * v;
+        ev[a][1] = -tv;
+        ev[a][2] = T(2) * tv + T(3) * v;
+        de[a][0] = T(2) * dt - T(3) * dv;
+        de[a][1] = -dt;
+        de[a][2] = T(2) * dt + T(3) * dv;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T dE = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            T q = T(0); // prod_{b<a} (1 + eps_b(v)) prod_{b>a} (1 + eps_b(u)) - 1
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+                if (b != a) {
+                    const T e = b < a ? ev[b][vel(D, i, b) + 1] : eu[b][vel(D, i, b) + 1];
+                    q = q + e + q * e;
+                }
+            const T d = de[a][vel(D, i, a) + 1];
+            dE += fma(d, q, d);
+        }
+        f[i] += (T(weight_k(D, i)) * r) * dE;
     }
 }
 

@@ -61,7 +61,7 @@ __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x
 #define ELBM_STEP_BOUNDS __launch_bounds__(kStepBlock)
 #endif
 
-template <class ST, bool kGrid3D>
+template <class ST, bool kGrid3D, bool kForce = false>
 __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
                                                     typename ST::S *__restrict__ fout, Geometry g,
                                                     CollideParams p)
@@ -91,6 +91,7 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
             f[i] = ST::load(__ldg(fin + off), T(weight(D, i)), rho0);
         }
         collide<D, T, true>(f, xd, p, &br);
+        if constexpr (kForce) add_force<D, T>(f, p);
         const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
         for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::store(f[i], T(weight(D, i)), rho0));
@@ -101,6 +102,7 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
         node_coords(n, g, x, y, z);
         pull_load<D, ST>(fin, g, x, y, z, rho0, f);
         collide<D, T, true>(f, xd, p, &br);
+        if constexpr (kForce) add_force<D, T>(f, p);
 #pragma unroll
         for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
     }
@@ -419,32 +421,50 @@ __global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restr
 // the transpose of pull streaming sends h_i(x) to node x - c_i (a push).
 // Gradient arrays are SoA [Q][N] in the compute type.
 // --------------------------------------------------------------------------
-template <class ST>
+template <class ST, bool kForce = false>
 __global__ void __launch_bounds__(kAuxBlock) k_step_adjoint(const typename ST::S *__restrict__ fin,
                                                            const typename ST::T *__restrict__ gnext,
                                                            typename ST::T *__restrict__ gout, Geometry g,
-                                                           CollideParams p)
+                                                           CollideParams p, double *__restrict__ dforce)
 {
     using T = typename ST::T;
     const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
-    if (n >= g.N) return;
-    int x, y, z;
-    node_coords(n, g, x, y, z);
-    T F[Q], gl[Q], h[Q];
-    pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), F);
+    T dfl[3] = {T(0), T(0), T(0)};
+    if (n < g.N) {
+        int x, y, z;
+        node_coords(n, g, x, y, z);
+        T F[Q], gl[Q], h[Q];
+        pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), F);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) gl[i] = gnext[(int64_t)i * g.N + n];
-    node_vjp<D, T>(F, gl, p, h);
-    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+        for (int i = 0; i < Q; ++i) gl[i] = gnext[(int64_t)i * g.N + n];
+        node_vjp<D, T, kForce>(F, gl, p, h, dfl);
+        const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
-        const int dx = cx == 1 ? xm : (cx == -1 ? xp : x);
-        const int dy = cy == 1 ? ym : (cy == -1 ? yp : y);
-        const int dz = cz == 1 ? zm : (cz == -1 ? zp : z);
-        gout[(int64_t)i * g.N + ((int64_t)dz * g.ny + dy) * g.nx + dx] = h[i];
+        for (int i = 0; i < Q; ++i) {
+            const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+            const int dx = cx == 1 ? xm : (cx == -1 ? xp : x);
+            const int dy = cy == 1 ? ym : (cy == -1 ? yp : y);
+            const int dz = cz == 1 ? zm : (cz == -1 ? zp : z);
+            gout[(int64_t)i * g.N + ((int64_t)dz * g.ny + dy) * g.nx + dx] = h[i];
+        }
+    }
+    if constexpr (kForce) {
+        // d/dF_b summed over the block (FP64), one atomic per block and component
+        __shared__ double s_df[kAuxBlock / 32][3];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const double v = warp_sum(double(dfl[a]));
+            if (lane == 0) s_df[warp][a] = v;
+        }
+        __syncthreads();
+        if (dforce && threadIdx.x < D) {
+            double v = 0.0;
+            for (int w = 0; w < kAuxBlock / 32; ++w) v += s_df[w][threadIdx.x];
+            atomicAdd(&dforce[threadIdx.x], v);
+        }
     }
 }
 
@@ -615,8 +635,10 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
 {
     using namespace ELBM_SUFFIX;
     if (g.N == 0) return cudaSuccess;
+    const bool forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
     // AUTO takes DIRECT: on GB300 it is the faster of the two at every size measured
-    // (D3Q27 256^3 FP32: 0.83 ms against 0.94 ms for ROWS).
+    // (D3Q27 256^3 FP32: 0.83 ms against 0.94 ms for ROWS).  The body force runs on DIRECT only.
+    if (kernel == ELBM_KERNEL_ROWS && forced) return cudaErrorNotSupported;
     if (kernel == ELBM_KERNEL_ROWS && ELBM_CAT(rows_kernel_applies, ELBM_SUFFIX)(storage, g)) {
         // the row pipeline is only instantiated for the FP32 and 16-bit storages
 #define ELBM_ROWS_FOR(STT)                                                                        \
@@ -639,13 +661,26 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
     if (kernel == ELBM_KERNEL_ROWS) return cudaErrorNotSupported;
     if (g.ny <= 65535 && g.nz <= 65535 && uint64_t(Q) * uint64_t(g.N) <= 0xffffffffull) {
         const dim3 grid(unsigned((g.nx + kStepBlock - 1) / kStepBlock), unsigned(g.ny), unsigned(g.nz));
-        ELBM_STORAGE_SWITCH(storage, (k_step<ST, true><<<grid, kStepBlock, 0, s>>>(
-                                         static_cast<const typename ST::S *>(fin),
-                                         static_cast<typename ST::S *>(fout), g, p)));
+        if (forced) {
+            ELBM_STORAGE_SWITCH(storage, (k_step<ST, true, true><<<grid, kStepBlock, 0, s>>>(
+                                             static_cast<const typename ST::S *>(fin),
+                                             static_cast<typename ST::S *>(fout), g, p)));
+        } else {
+            ELBM_STORAGE_SWITCH(storage, (k_step<ST, true><<<grid, kStepBlock, 0, s>>>(
+                                             static_cast<const typename ST::S *>(fin),
+                                             static_cast<typename ST::S *>(fout), g, p)));
+        }
     } else {
-        ELBM_STORAGE_SWITCH(storage, (k_step<ST, false><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
-                                         static_cast<const typename ST::S *>(fin),
-                                         static_cast<typename ST::S *>(fout), g, p)));
+        if (forced) {
+            ELBM_STORAGE_SWITCH(storage,
+                                (k_step<ST, false, true><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
+                                    static_cast<const typename ST::S *>(fin),
+                                    static_cast<typename ST::S *>(fout), g, p)));
+        } else {
+            ELBM_STORAGE_SWITCH(storage, (k_step<ST, false><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
+                                             static_cast<const typename ST::S *>(fin),
+                                             static_cast<typename ST::S *>(fout), g, p)));
+        }
     }
     return cudaGetLastError();
 }
@@ -672,14 +707,22 @@ cudaError_t ELBM_CAT(launch_step_batch, ELBM_SUFFIX)(int storage, const void *fi
 
 cudaError_t ELBM_CAT(launch_step_adjoint, ELBM_SUFFIX)(int storage, const void *fin, const void *gnext,
                                                        void *gout, const Geometry &g, const CollideParams &p,
-                                                       cudaStream_t s)
+                                                       double *dforce, cudaStream_t s)
 {
     using namespace ELBM_SUFFIX;
     if (g.N == 0) return cudaSuccess;
-    ELBM_STORAGE_SWITCH(storage, (k_step_adjoint<ST><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
-                                     static_cast<const typename ST::S *>(fin),
-                                     static_cast<const typename ST::T *>(gnext), static_cast<typename ST::T *>(gout),
-                                     g, p)));
+    const bool forced = dforce || p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
+    if (forced) {
+        ELBM_STORAGE_SWITCH(storage, (k_step_adjoint<ST, true><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
+                                         static_cast<const typename ST::S *>(fin),
+                                         static_cast<const typename ST::T *>(gnext),
+                                         static_cast<typename ST::T *>(gout), g, p, dforce)));
+    } else {
+        ELBM_STORAGE_SWITCH(storage, (k_step_adjoint<ST><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
+                                         static_cast<const typename ST::S *>(fin),
+                                         static_cast<const typename ST::T *>(gnext),
+                                         static_cast<typename ST::T *>(gout), g, p, nullptr)));
+    }
     return cudaGetLastError();
 }
 

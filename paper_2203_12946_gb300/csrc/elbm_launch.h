@@ -69,7 +69,7 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
                                            int bx, const CollideParams &p, cudaStream_t s);          \
     cudaError_t launch_step_adjoint_##SUFFIX(int storage, const void *fin, const void *gnext,       \
                                              void *gout, const Geometry &g, const CollideParams &p,  \
-                                             cudaStream_t s);                                        \
+                                             double *dforce, cudaStream_t s);                        \
     cudaError_t launch_kinetic_energy_##SUFFIX(int storage, const void *f, const Geometry &g,       \
                                                double rho0, double *acc, void *grad, int num_sms,    \
                                                cudaStream_t s);                                      \

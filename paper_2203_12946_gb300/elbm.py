@@ -51,7 +51,7 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
             "elbm_batch_init_equilibrium", "elbm_batch_step", "elbm_batch_tune", "elbm_batch_moments",
             "elbm_batch_diagnostics", "elbm_batch_get_populations", "elbm_batch_set_populations",
             "elbm_batch_synchronize", "elbm_adjoint_step", "elbm_kinetic_energy", "elbm_equilibrium_vjp",
-            "elbm_subgrid_viscosity"]
+            "elbm_subgrid_viscosity", "elbm_adjoint_step_force", "elbm_set_force"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -142,6 +142,8 @@ def load(build_if_missing: bool = True):
             "elbm_kinetic_energy": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_double), P]),
             "elbm_equilibrium_vjp": (ctypes.c_int, [P, P, P, P, P, P]),
             "elbm_subgrid_viscosity": (ctypes.c_int, [P, P, ctypes.c_int]),
+            "elbm_adjoint_step_force": (ctypes.c_int, [P, P, P, P, P]),
+            "elbm_set_force": (ctypes.c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -267,6 +269,16 @@ def elbm_diagnostics_noalloc(lattice, dims, beta, populations, opts: elbm_opts |
 
 def elbm_subgrid_viscosity(h, nut_out, where=ELBM_MEM_DEVICE) -> None:
     _check(h, load().elbm_subgrid_viscosity(h, _ptr(nut_out), int(where)), "elbm_subgrid_viscosity")
+
+
+def elbm_adjoint_step_force(h, f_t, g_next, g_t, dforce) -> None:
+    _check(h, load().elbm_adjoint_step_force(h, _ptr(f_t), _ptr(g_next), _ptr(g_t), _ptr(dforce)),
+           "elbm_adjoint_step_force")
+
+
+def elbm_set_force(h, force) -> None:
+    arr = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    _check(h, load().elbm_set_force(h, None if arr is None else arr.ctypes.data), "elbm_set_force")
 
 
 def elbm_adjoint_step(h, f_t, g_next, g_t) -> None:
@@ -440,9 +452,18 @@ class Simulation:
     def restore(self, buf):
         elbm_set_populations(self.h, buf, ELBM_MEM_DEVICE)
 
-    def adjoint_step(self, f_t, g_next):
+    def set_force(self, force=None):
+        """Uniform body force (D values, or None for none); see elbm_set_force."""
+        elbm_set_force(self.h, None if force is None else np.asarray(force, dtype=np.float64).ravel()[:self.D])
+
+    def adjoint_step(self, f_t, g_next, dforce=None):
+        """One reverse step; with ``dforce`` (a float64 device tensor of D values) also
+        accumulates the derivative with respect to the body force into it."""
         g_t = self.torch.empty_like(g_next)
-        elbm_adjoint_step(self.h, f_t, g_next, g_t)
+        if dforce is None:
+            elbm_adjoint_step(self.h, f_t, g_next, g_t)
+        else:
+            elbm_adjoint_step_force(self.h, f_t, g_next, g_t, dforce)
         return g_t
 
     def kinetic_energy(self, f=None, with_grad=False):

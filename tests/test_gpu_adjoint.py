@@ -173,3 +173,99 @@ def test_rollout_gradient_against_oracle_adjoint():
             gg = sim.adjoint_step(st[t], gg)
         got = gg.cpu().numpy()
     assert np.linalg.norm(got - g) / np.linalg.norm(g) < 1e-7
+
+
+# ---------------------------------------------------------------------------
+# Uniform body force (exact-difference term after the collision; not in the paper)
+# ---------------------------------------------------------------------------
+
+FORCE = {2: np.array([2e-4, -1e-4]), 3: np.array([2e-4, -1e-4, 3e-4])}
+
+
+@pytest.mark.parametrize("D,dims", [(2, (29, 17, 1)), (3, (11, 9, 7))])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 4e-6)])
+def test_forced_step_matches_oracle(D, dims, storage, tol):
+    beta = 0.99
+    f0 = noisy(D, dims, 3e-3, seed=61)
+    if storage == "f32":
+        f0 = f0.astype(np.float32).astype(np.float64)
+    want, *_ = O.step(D, dims, f0, beta, cutoff=False, nsteps=3, force=FORCE[D])
+    with E.Simulation(LAT[D], dims, beta, storage=storage, cutoff=False) as sim:
+        sim.set_populations(f0)
+        sim.set_force(FORCE[D])
+        sim.step(3)
+        got = sim.get_populations().astype(np.float64)
+    assert np.max(np.abs(got - want) / want) < tol
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 2e-7)])
+def test_uniform_flow_accelerates_on_gpu(storage, tol):
+    """u(t) = u0 + t F / rho for a uniform equilibrium under the force (exact in the method)."""
+    D, dims = 3, (8, 6, 5)
+    N = int(np.prod(dims))
+    u0 = np.array([0.01, -0.02, 0.015])
+    with E.Simulation(E.ELBM_D3Q27, dims, 0.95, storage=storage) as sim:
+        sim.init_equilibrium(np.full(N, 1.02), np.repeat(u0[:, None], N, axis=1))
+        sim.set_force(FORCE[3])
+        sim.step(40)
+        r, u = [t.cpu().numpy() for t in sim.moments()]
+    assert np.max(np.abs(u - (u0 + 40 * FORCE[3] / 1.02)[:, None])) < tol
+    assert np.max(np.abs(r - 1.02)) < tol
+
+
+@pytest.mark.parametrize("D,dims", [(2, (13, 11, 1)), (3, (6, 5, 4))])
+def test_forced_adjoint_step_matches_oracle(D, dims):
+    import torch
+
+    beta = 0.99
+    f = noisy(D, dims, 5e-3, seed=67)
+    g = np.random.default_rng(68).standard_normal(f.shape)
+    want = O.step_adjoint(D, dims, f, g, beta, cutoff=False, force=FORCE[D])
+    want_F = O.step_force_vjp(D, dims, f, g, beta, FORCE[D])
+    with E.Simulation(LAT[D], dims, beta, storage="f64", cutoff=False) as sim:
+        sim.set_populations(f)
+        sim.set_force(FORCE[D])
+        dF = torch.zeros(D, dtype=torch.float64, device="cuda")
+        got = sim.adjoint_step(sim.state_copy(), torch.from_numpy(g).cuda(), dforce=dF).cpu().numpy()
+        dF = dF.cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-7
+    assert np.max(np.abs(dF - want_F)) < 1e-6 * np.max(np.abs(want_F))
+
+
+@pytest.mark.parametrize("storage,tol,mean", [("f64", 1e-6, 0.0), ("f32", 1e-4, 0.01)])
+def test_rollout_force_gradient_against_finite_differences(storage, tol, mean):
+    """dL/dF from the checkpointed reverse sweep against central differences of the FP64
+    forward in each component of F, at F = 0 and at a nonzero F.  For a zero-mean vortex
+    dL/dF is close to the time-integrated total momentum, a sum over nodes that cancels to
+    ~1e-5 of its terms, below what FP32 node sums resolve; the FP32 case adds a mean flow."""
+    import torch
+
+    from paper_2203_12946_gb300.adjoint import kinetic_energy_rollout
+
+    L, beta, T = 32, 0.95, 40
+    dims = (L, L, 1)
+    rho0, u0 = inputs.random_vortex_2d(L, rms=0.02, seed=5)
+    u0 = u0 + np.array([mean, -0.5 * mean])[:, None]
+    for F in (np.zeros(2), np.array([1e-4, -2e-4])):
+        with E.Simulation(E.ELBM_D2Q9, dims, beta, storage=storage, cutoff=False) as sim:
+            ut = torch.from_numpy(u0).cuda().requires_grad_(True)
+            Ft = torch.from_numpy(F.copy()).requires_grad_(True)
+            kinetic_energy_rollout(ut, sim, T, rho0=torch.from_numpy(rho0).cuda(), force=Ft).backward()
+            dF = Ft.grad.numpy()
+        for a in range(2):
+            # L is far from linear in F (its curvature ~ N T^2), so the central differences
+            # are Richardson-extrapolated from steps h and h/2 (error O(h^4)).
+            fds = []
+            for h in (2e-6, 1e-6):
+                Ls = []
+                for sgn in (1, -1):
+                    Fp = F.copy()
+                    Fp[a] += sgn * h
+                    with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64", cutoff=False) as sim:
+                        sim.init_equilibrium(rho0, u0)
+                        sim.set_force(Fp)
+                        sim.step(T)
+                        Ls.append(sim.kinetic_energy())
+                fds.append((Ls[0] - Ls[1]) / (2 * h))
+            fd = (4 * fds[1] - fds[0]) / 3
+            assert abs(dF[a] - fd) <= tol * abs(fd), (a, dF[a], fd, fds)
