@@ -602,8 +602,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-slab", type=int, default=32)
-    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--cpu-slab", type=int, default=128,
+                    help="z-extent of the 256x256 slab the CPU oracle times (about 10-30 s of work)")
+    ap.add_argument("--cpu-steps", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "direct", "rows"], default="auto")
     ap.add_argument("--workload", choices=["tgv3d", "ensemble", "precision", "adjoint"], default="tgv3d",
