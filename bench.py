@@ -502,6 +502,49 @@ def run_precision(args):
     return 0
 
 
+def run_storage(args):
+    """Storage forms on the benchmark flow: D3Q27 L^3 Taylor-Green vortex (u0 = 0.05,
+    beta = 0.999) from the same initial state in FP64, FP32, FP16 and BF16 deviation storage;
+    step time from CUDA events over steps 10..K (K = --storage-steps) and the velocity error
+    of the final state against the FP64 run."""
+    import torch
+
+    from paper_2203_12946_gb300 import elbm as E
+    from paper_2203_12946_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    K = args.storage_steps
+    dims = (L, L, L)
+    X, Y, Z = inputs.grid(dims)
+    rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=U0)
+    res = {}
+    for st in ("f64", "f32", "f16dev", "bf16dev"):
+        with E.Simulation(E.ELBM_D3Q27, dims, BETA, storage=st) as sim:
+            sim.init_equilibrium(rho, u)
+            sim.step(10)
+            stream = torch.cuda.current_stream()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            sim.step(K - 10)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / (K - 10)
+            _, uu = sim.moments()
+            res[st] = (ms, uu.cpu().numpy())
+    u64 = res["f64"][1]
+    out = {}
+    for st, (ms, uu) in res.items():
+        out[st] = {"ms_per_step": ms, "mlups": L ** 3 / ms / 1e3,
+                   "u_rel_l2_vs_f64": float(np.linalg.norm(uu - u64) / np.linalg.norm(u64)),
+                   "u_linf_over_u0": float(np.max(np.abs(uu - u64)) / U0)}
+    line = {"metric": "step time and velocity error vs FP64 per storage, D3Q27 Taylor-Green vortex",
+            "config": {"workload": "storage forms", "dims": [L, L, L], "beta": BETA, "u0": U0, "steps": K},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_adjoint(args):
     """Gradient of the final kinetic energy with respect to the initial velocity field and
     to a uniform body force F (evaluated at F = 0): D2Q9 256^2 periodic, beta = 0.9, u0
@@ -607,14 +650,17 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "direct", "rows"], default="auto")
-    ap.add_argument("--workload", choices=["tgv3d", "ensemble", "precision", "adjoint"], default="tgv3d",
+    ap.add_argument("--workload", choices=["tgv3d", "ensemble", "precision", "adjoint", "storage"],
+                    default="tgv3d",
                     help="tgv3d: the benchmark (D3Q27 256^3); ensemble: batched D2Q9 domains; "
-                         "precision: storage error study on the D2Q9 shear layer")
+                         "precision: storage error study on the D2Q9 shear layer; adjoint: gradient "
+                         "rollout; storage: storage forms on the D3Q27 flow")
     ap.add_argument("--shear-L", type=int, default=1024)
     ap.add_argument("--checkpoints", default="1000,5000,20000")
     ap.add_argument("--oracle-steps", type=int, default=50)
     ap.add_argument("--adjoint-L", type=int, default=256)
     ap.add_argument("--fd-dirs", type=int, default=4)
+    ap.add_argument("--storage-steps", type=int, default=1000)
     ap.add_argument("--storage", choices=["f32", "f16dev", "bf16dev"], default=STORAGE)
     ap.add_argument("--L", type=int, default=L, help="domain side (profiling runs only; "
                     "the benchmark workload is 256)")
@@ -631,6 +677,8 @@ def main():
         return run_precision(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "storage":
+        return run_storage(args)
     return run_gpu(args)
 
 
