@@ -100,11 +100,9 @@ __device__ __forceinline__ float rcp_(float b)
 }
 __device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
 // 1/rho for the velocity u = j/rho: the approximate reciprocal followed by one
-// Newton-Raphson step for 1/b (r + r (1 - b r)).  The approximation alone is off
-// by a fraction of an ulp with the same sign for every rho near 1, which scales
-// the equilibrium momentum by the same factor at every node and step and builds
-// up in long runs (FP32 kinetic energy drifted by 5e-5 in 2000 steps at
-// beta = 0.9); after the step the error is a rounding error with no preferred sign.
+// Newton-Raphson step for 1/b (r + r (1 - b r)), which brings it to within about
+// half an ulp; u carries every other quantity of the node, so it gets the
+// accurate reciprocal for two extra fused multiply-adds per node.
 __device__ __forceinline__ float rcp_nr(float b)
 {
     const float r = rcp_(b);
