@@ -244,6 +244,13 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
     double sum[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long cnt[5] = {0, 0, 0, 0, 0};
     unsigned long long dmax = 0ULL, amin = ~0ULL, amax = 0ULL;
+    // Per-thread partial sums in the compute type of the small parts (deviations, H + 1,
+    // alpha - 2) over the thread's few dozen nodes; the exact parts (one per node, 2 per
+    // alpha) and the conversion to FP64 are added once per thread below (FP64 arithmetic
+    // is slow on this GPU, and per node it was a third of the kernel's work).
+    T p_dr = T(0), p_j[3] = {T(0), T(0), T(0)}, p_h = T(0), p_al = T(0);
+    T p_dmax = -INFINITY, p_amin = INFINITY, p_amax = -INFINITY;
+    unsigned long long p_nodes = 0, p_hnodes = 0;
 
     for (int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; n < g.N;
          n += (int64_t)gridDim.x * kAuxBlock) {
@@ -260,10 +267,8 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         }
         int br;
         const T alpha_t = collide<D, T, false>(f, xd, p, &br);
-        const double alpha = double(alpha_t);
 
-        // Mass and momentum through the deviations d_i = f_i - w_i (small numbers,
-        // summed per node in T), then per node into the FP64 domain sums.
+        // Mass and momentum through the deviations d_i = f_i - w_i (small numbers).
         T dr = T(0), jt[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -272,8 +277,9 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
 #pragma unroll
             for (int a = 0; a < D; ++a) jt[a] += T(vel(D, i, a)) * di;
         }
-        sum[0] += 1.0 + weight_sum_error<D, T>() + double(dr);
-        for (int a = 0; a < D; ++a) sum[1 + a] += double(jt[a]);
+        p_nodes += 1;
+        p_dr += dr;
+        for (int a = 0; a < D; ++a) p_j[a] += jt[a];
         if (bad) {
             cnt[3] += 1;
         } else {
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
                 s3 += fi * xi * xi;
                 xa = fmax(xa, fabs(xi));
             }
-            double dH;
+            T dH;
             if (xa < T(0.1) && ab <= T(2.2)) {
                 // g(ab x) - ab x log(1+x) = sum_{k>=2} c_k x^k,
                 // c_k = (-1)^k ab/(k-1) (ab^(k-1)/k - 1), summed to k = kTop (for |x| < 0.1
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
                     for (int k = kTop - 1; k >= 2; --k) poly = fma(poly, xi, ck[k]);
                     sd += fc[i] * (poly * xi * xi);
                 }
-                dH = double(sd);
+                dH = sd;
             } else {
                 T s1 = T(0), s2 = T(0);
 #pragma unroll
@@ -326,22 +332,39 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
                     s1 += fi * g_entropy<T>(ab * xi);
                     s2 += fi * xi * log1p(xi);
                 }
-                dH = double(s1) - double(ab) * double(s2);
+                dH = s1 - ab * s2;
             }
-            sum[4] += double(hl) - (1.0 + weight_sum_error<D, T>() + double(dr));
-            dmax = max(dmax, ordered_bits(dH));
-            if (dH > 1e-6 * double(s3) && s3 > T(0)) cnt[4] += 1;
+            // H of the node + (1 + e_w) (the node's -rho without its exact part)
+            p_h += hl - dr;
+            p_hnodes += 1;
+            p_dmax = fmax(p_dmax, dH);
+            if (dH > T(1e-6) * s3 && s3 > T(0)) cnt[4] += 1;
         }
-        sum[5] += alpha;
+        p_al += alpha_t - T(2);
         cnt[br == kBranchCutoff ? 0 : (br == kBranchSolved ? 1 : 2)] += 1;
-        const unsigned long long ao = ordered_bits(alpha);
-        amin = min(amin, ao);
-        amax = max(amax, ao);
+        p_amin = fmin(p_amin, alpha_t);
+        p_amax = fmax(p_amax, alpha_t);
+        // bin of alpha on [1.9, 2.1): alpha - 1.9 with 1.9 in two parts of T
+        constexpr T kLo = T(1.9), kLo2 = T(1.9 - double(T(1.9)));
+        const T off = (alpha_t - kLo) - kLo2;
         int bin;
-        if (!(alpha >= 1.9)) bin = 0;
-        else if (alpha >= 2.1) bin = ELBM_HIST_BINS + 1;
-        else bin = 1 + min(ELBM_HIST_BINS - 1, int((alpha - 1.9) * (ELBM_HIST_BINS / 0.2)));
+        if (!(off >= T(0))) bin = 0;
+        else if (off >= T(0.2)) bin = ELBM_HIST_BINS + 1;
+        else bin = 1 + min(ELBM_HIST_BINS - 1, int(off * T(ELBM_HIST_BINS / 0.2)));
         atomicAdd(&s_hist[bin], 1u);
+    }
+    // this thread's nodes into the FP64 sums: mass = sum (1 + e_w + dr), H = sum hl - rho
+    {
+        const double nn = double(p_nodes), one = 1.0 + weight_sum_error<D, T>();
+        sum[0] = nn * one + double(p_dr);
+        for (int a = 0; a < D; ++a) sum[1 + a] = double(p_j[a]);
+        sum[4] = double(p_h) - double(p_hnodes) * one;
+        sum[5] = 2.0 * nn + double(p_al);
+        if (p_nodes) {
+            dmax = p_hnodes ? ordered_bits(double(p_dmax)) : 0ULL;
+            amin = ordered_bits(double(p_amin));
+            amax = ordered_bits(double(p_amax));
+        }
     }
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
