@@ -326,7 +326,12 @@ def run_gpu(args):
     kern_avg = float(np.mean(kern))
     elapsed = rep.max(elapsed)
     gpu_launches = args.steps + args.steps // DIAG_EVERY
-    d = sim.diagnostics()
+    d = sim.diagnostics(with_hist=True)
+    hist = d["alpha_hist"]
+    edges = np.linspace(1.9, 2.1, E.ELBM_HIST_BINS + 1)
+    nz = np.nonzero(hist[1:-1])[0]
+    alpha_hist = {"range": [1.9, 2.1], "bins": E.ELBM_HIST_BINS, "below": int(hist[0]), "above": int(hist[-1]),
+                  "nonzero_bins": {"%.5f" % edges[b]: int(hist[1 + b]) for b in nz}}
 
     # End to end through the C ABI with host buffers: initial rho/u uploaded from pinned
     # host memory, K steps (with the diagnostics cadence), rho/u read back to host.
@@ -370,9 +375,11 @@ def run_gpu(args):
                 "what": "elbm_init_equilibrium from pinned host rho,u + K steps + elbm_moments to host"},
         "gpu_launches": gpu_launches,
         "clocks": clk,
-        "physics": {"alpha_min": d["alpha_min"], "alpha_max": d["alpha_max"],
-                    "n_solved_frac": d["n_solved"] / N, "n_clamped": d["n_clamped"],
-                    "n_nonpositive": d["n_nonpositive"]},
+        "physics": {"alpha_min": d["alpha_min"], "alpha_max": d["alpha_max"], "alpha_mean": d["alpha_mean"],
+                    "n_solved_frac": d["n_solved"] / N, "n_cutoff_frac": d["n_cutoff"] / N,
+                    "n_clamped": d["n_clamped"], "n_nonpositive": d["n_nonpositive"],
+                    "dH_max": d["dH_max"], "n_dH_positive": d["n_dH_positive"],
+                    "mass": d["mass"], "H": d["H"], "alpha_hist": alpha_hist},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, dt, desc = oracle_time(*oracle_prepare(args.cpu_slab), args.cpu_steps)

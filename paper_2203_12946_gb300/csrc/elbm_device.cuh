@@ -538,28 +538,71 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
     int br = kBranchCutoff;
     if (p.mode != kModeLBGK && !(p.cutoff && xabs < float(kCutoff))) {
         // Eq. alphaLowerCoeffs and the x-only parts of Eq. qaud_tight_coeff, and the
-        // Omega- power sums S3..S6 (as in node_collide).
-        float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f);
-        float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
+        // Omega- power sums S3..S6 (as in node_collide).  Where |x|max < kSeriesX the
+        // three rational terms are summed from power sums M_k = <f, x^k> (all i) and
+        // S_k (Omega-), their series truncated below FP32 rounding:
+        //   2/(2 + x) = sum_k (-x/2)^k                     (c1 = <f, x^2 2/(2+x)>)
+        //   (60 + 60x + 11x^2)/(60 + 90x + 36x^2 + 3x^3)
+        //       = 1 - x/2 + x^2/3 - x^3/4 + x^4/5 - ...      (c; log(1+x)/x to x^5)
+        //   2/(4+t) + 1/(4+2t) + 2/(4+3t) = 5/4 - 5t/8 + 3t^2/8 - t^3/4 + ...   (b, t = k x)
+        // with the Omega+ sums P_m = M_m - S_m.  Kept to M6: at |x| = 0.02 the dropped
+        // terms are ~1e-10 of c1 and c and ~4e-9 of b.  The series form needs no
+        // reciprocal per population and no second pass for b.
+        constexpr float kSeriesX = 0.02f;
+        const bool series = xabs < kSeriesX;
+        float sb1, sc1, sc, s3, s4, s5, s6, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f, m6 = 0.0f;
+        if (series) {
+            float2 M2 = f2(0.0f), M3 = f2(0.0f), M4 = f2(0.0f), M5 = f2(0.0f), M6 = f2(0.0f);
+            float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const float2 xi = xp[k];
-            const float2 fx2 = pmul(pmul(fp[k], xi), xi); // f x^2
-            const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
-            const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
-            b1 = padd(b1, fx2);
-            c1 = pfma(A, K, c1);
-            c = pfma(pmul(A, xi), xi, c); // c = c1 + 5 <f, A x^2> below
-            const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
-            const float2 q = pmul(fx2, xm); // f x^3 on Omega-, 0 elsewhere
-            const float2 xm2 = pmul(xm, xm);
-            S3 = padd(S3, q);
-            S4 = pfma(q, xm, S4);
-            S5 = pfma(q, xm2, S5);
-            S6 = pfma(pmul(q, xm), xm2, S6);
+            for (int k = 0; k < NP; ++k) {
+                const float2 xi = xp[k];
+                const float2 x2 = pmul(xi, xi);
+                const float2 fx2 = pmul(fp[k], x2); // f x^2
+                const float2 q3 = pmul(fx2, xi);
+                const float2 q5 = pmul(q3, x2);
+                M2 = padd(M2, fx2);
+                M3 = padd(M3, q3);
+                M4 = pfma(q3, xi, M4);
+                M5 = padd(M5, q5);
+                M6 = pfma(q5, xi, M6);
+                const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+                const float2 q = pmul(fx2, xm); // f x^3 on Omega-, 0 elsewhere
+                const float2 xm2 = pmul(xm, xm);
+                S3 = padd(S3, q);
+                S4 = pfma(q, xm, S4);
+                S5 = pfma(q, xm2, S5);
+                S6 = pfma(pmul(q, xm), xm2, S6);
+            }
+            const float m2 = M2.x + M2.y;
+            m3 = M3.x + M3.y, m4 = M4.x + M4.y, m5 = M5.x + M5.y, m6 = M6.x + M6.y;
+            sb1 = 0.5f * m2;
+            sc1 = m2 + (m3 * -0.5f + (m4 * 0.25f + (m5 * -0.125f + m6 * 0.0625f))); // <f, 2x^2/(2+x)>
+            sc = m2 + (m3 * -0.5f + (m4 * (1.0f / 3.0f) + (m5 * -0.25f + m6 * 0.2f)));
+            s3 = S3.x + S3.y, s4 = S4.x + S4.y, s5 = S5.x + S5.y, s6 = S6.x + S6.y;
+        } else {
+            float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f);
+            float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float2 xi = xp[k];
+                const float2 fx2 = pmul(pmul(fp[k], xi), xi); // f x^2
+                const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
+                const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
+                b1 = padd(b1, fx2);
+                c1 = pfma(A, K, c1);
+                c = pfma(pmul(A, xi), xi, c); // c = c1 + 5 <f, A x^2> below
+                const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+                const float2 q = pmul(fx2, xm); // f x^3 on Omega-, 0 elsewhere
+                const float2 xm2 = pmul(xm, xm);
+                S3 = padd(S3, q);
+                S4 = pfma(q, xm, S4);
+                S5 = pfma(q, xm2, S5);
+                S6 = pfma(pmul(q, xm), xm2, S6);
+            }
+            sb1 = 0.5f * (b1.x + b1.y), sc1 = 2.0f * (c1.x + c1.y), sc = sc1 + 5.0f * (c.x + c.y);
+            s3 = S3.x + S3.y, s4 = S4.x + S4.y, s5 = S5.x + S5.y, s6 = S6.x + S6.y;
         }
-        const float sb1 = 0.5f * (b1.x + b1.y), sc1 = 2.0f * (c1.x + c1.y), sc = sc1 + 5.0f * (c.x + c.y);
-        const float s3 = S3.x + S3.y, s4 = S4.x + S4.y, s5 = S5.x + S5.y, s6 = S6.x + S6.y;
         if (sb1 > 0.0f) {
             const float aL = quad_root(0.5f * s3, sb1, sc1); // alpha_Lower
             if (p.mode == kModeLower) {
@@ -567,18 +610,25 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
             } else {
                 // b: Omega+ Boole term with k = alpha_L beta (derived) or alpha_L (printed).
                 const float kk = p.b_variant ? aL : aL * beta;
-                float2 bp = f2(0.0f);
+                float bsum;
+                if (series) {
+                    const float p3 = m3 - s3, p4 = m4 - s4, p5 = m5 - s5, p6 = m6 - s6;
+                    bsum = 1.25f * p3 + kk * (-0.625f * p4 + kk * (0.375f * p5 + kk * (-0.25f * p6)));
+                } else {
+                    float2 bp = f2(0.0f);
 #pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    const float2 xi = xp[k];
-                    const float2 xq = f2(fmaxf(xi.x, 0.0f), fmaxf(xi.y, 0.0f));
-                    const float2 t = pmul(f2(kk), xq);
-                    const float2 nu = pfma(pfma(f2(19.0f), t, f2(80.0f)), t, f2(80.0f));
-                    const float2 de = pfma(pfma(pfma(f2(6.0f), t, f2(44.0f)), t, f2(96.0f)), t, f2(64.0f));
-                    // f x^3 on Omega+ (0 elsewhere) times the bracket
-                    bp = pfma(pmul(pmul(fp[k], pmul(pmul(xi, xi), xq)), nu), prcp(de), bp);
+                    for (int k = 0; k < NP; ++k) {
+                        const float2 xi = xp[k];
+                        const float2 xq = f2(fmaxf(xi.x, 0.0f), fmaxf(xi.y, 0.0f));
+                        const float2 t = pmul(f2(kk), xq);
+                        const float2 nu = pfma(pfma(f2(19.0f), t, f2(80.0f)), t, f2(80.0f));
+                        const float2 de = pfma(pfma(pfma(f2(6.0f), t, f2(44.0f)), t, f2(96.0f)), t, f2(64.0f));
+                        // f x^3 on Omega+ (0 elsewhere) times the bracket
+                        bp = pfma(pmul(pmul(fp[k], pmul(pmul(xi, xi), xq)), nu), prcp(de), bp);
+                    }
+                    bsum = bp.x + bp.y;
                 }
-                const float b = sb1 - (2.0f / 15.0f) * aL * beta * beta * (bp.x + bp.y);
+                const float b = sb1 - (2.0f / 15.0f) * aL * beta * beta * bsum;
                 const float h = quad_root(beta * beta * s3 * (1.0f / 6.0f), b, sc);
                 const float hb = h * beta;
                 const float a = beta * beta *

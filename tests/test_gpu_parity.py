@@ -169,6 +169,28 @@ def test_fp32_single_step(D, dims, cutoff):
     assert np.max(rel[:, agree]) < 2e-6
 
 
+@pytest.mark.parametrize("D,dims", [(2, (211, 53, 1)), (3, (31, 17, 13))])
+def test_fp32_series_and_exact_paths(D, dims):
+    """Noise levels whose |x|max straddles 0.02, where the FP32 collision switches between
+    power-series and per-population forms of its coefficients: both agree with the oracle
+    at FP32 precision, and nodes on either side are present."""
+    beta = 0.995
+    f0 = noisy_state(D, dims, 0.016 if D == 2 else 0.012, seed=43).astype(np.float32)
+    f_in = f0.astype(np.float64)
+    f_gpu = gpu_run(D, dims, beta, f0, 1, "f32", cutoff=True)
+    f_pre = O.stream(D, dims, f_in)
+    f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=True, want_alpha=True)
+    xm = xabsmax_of(D, f_pre)
+    assert np.sum(xm < 0.019) > 50 and np.sum(xm > 0.021) > 50
+    with E.Simulation(LAT[D], dims, beta, storage="f32", cutoff=True) as sim:
+        sim.set_populations(f0)
+        a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]
+    agree = check_branches(D, f_pre, fl, br_ora, 1e-6)
+    assert np.max(np.abs(a_gpu[agree] - a_ora[agree])) < 2e-5
+    rel = np.abs(f_gpu - f_ora) / f_ora
+    assert np.max(rel[:, agree]) < 2e-6
+
+
 @pytest.mark.parametrize("D,dims", [(2, (131, 29, 1)), (3, (21, 13, 9))])
 def test_fp32_iterate1_mode(D, dims):
     """alpha_Iterate1 (Sec. IV) in FP32 against the oracle, including nodes far enough
