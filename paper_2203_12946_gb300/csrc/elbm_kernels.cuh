@@ -51,15 +51,25 @@ __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x
 // y = blockIdx.y, z = blockIdx.z: no index arithmetic, 32-bit offsets) or, when
 // ny or nz exceed the grid limits or Q N reaches 2^32, on a 1D grid over all nodes.
 // Minimum resident blocks per SM requested from the register allocator for the
-// direct step kernel (0: let the compiler choose).
+// direct step kernel.  D3Q27 with FP32 storage: 7 blocks of 128 (72 registers).
+// Near equilibrium the step is bound by load latency, and the extra resident warps
+// outweigh the spills, which fall in the per-population form of the coefficients
+// (large |x| only): 0.640 -> 0.627 ms per 256^3 step on GB300.  The 16-bit storages
+// lose with that cap (their loads and stores need more live values): 5 blocks, the
+// allocation they had unbounded.  D2Q9 with FP32 arithmetic: 4 blocks of 256 (at most
+// 64 registers).  FP64 (the parity path): no bound.  ELBM_STEP_MIN_BLOCKS overrides.
 #ifndef ELBM_STEP_MIN_BLOCKS
 #define ELBM_STEP_MIN_BLOCKS 0
 #endif
-#if ELBM_STEP_MIN_BLOCKS > 0
-#define ELBM_STEP_BOUNDS __launch_bounds__(kStepBlock, ELBM_STEP_MIN_BLOCKS)
-#else
-#define ELBM_STEP_BOUNDS __launch_bounds__(kStepBlock)
-#endif
+template <class ST>
+constexpr int step_min_blocks()
+{
+    return ELBM_STEP_MIN_BLOCKS > 0 ? ELBM_STEP_MIN_BLOCKS
+                                    : (sizeof(typename ST::T) != 4 ? 1
+                                       : D == 2                  ? 4
+                                       : sizeof(typename ST::S) == 4 ? 7 : 5);
+}
+#define ELBM_STEP_BOUNDS __launch_bounds__(kStepBlock, step_min_blocks<ST>())
 
 template <class ST, bool kGrid3D, bool kForce = false>
 __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
