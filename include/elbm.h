@@ -228,6 +228,16 @@ int elbm_subgrid_viscosity(elbm_t *h, double *nut_out, int where);
  * <= 0 or not finite. */
 int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist);
 
+/* n >= 1 steps (as elbm_step) whose first step also takes the diagnostics of
+ * elbm_diagnostics: *out and alpha_hist describe the state before the n steps
+ * and the collision its first step applies (Eq. hdef, Eq. deltaH3), as
+ * elbm_diagnostics called before elbm_step(h, n) would, up to the order of
+ * floating-point sums.  On the DIRECT kernel without body force the first
+ * step and the diagnostics are one pass over the populations; otherwise the
+ * diagnostics pass runs first.  Synchronises the stream.  Errors: as
+ * elbm_diagnostics and elbm_step; ELBM_ERR_ARG for n < 1. */
+int elbm_step_diag(elbm_t *h, int64_t n, elbm_diag *out, int64_t *alpha_hist);
+
 /* Copies the current population buffer (Q*N storage elements, layout above)
  * to dst / from src.  where selects host or device memory.  Host copies
  * synchronise the stream.  set resets the step counter. */

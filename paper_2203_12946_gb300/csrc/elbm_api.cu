@@ -479,23 +479,24 @@ int elbm_subgrid_viscosity(elbm_t *h, double *nut_out, int where)
     return ELBM_OK;
 }
 
-int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist)
+namespace {
+
+// Clears the handle's diagnostics accumulator (on its stream).
+cudaError_t clear_diag_acc(elbm_t *h)
 {
-    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_diagnostics: handle is NULL");
-    if (!out) return fail(h, ELBM_ERR_ARG, "elbm_diagnostics: out is NULL");
-    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_diagnostics: no state");
-    DeviceGuard guard(h->opts.device);
     cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(DiagAcc), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&h->acc->amin_ord, 0xFF, sizeof(unsigned long long), h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: clear scratch");
-    e = ELBM_BY_LATTICE(h, launch_diag, h->opts.storage, h->pop[h->cur], h->g, params_of(h), h->acc, h->num_sms,
-                        h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: kernel launch");
+    return e;
+}
+
+// Reads the accumulator back (synchronising the stream) and fills *out / alpha_hist.
+int read_diag_acc(elbm_t *h, elbm_diag *out, int64_t *alpha_hist, const char *what)
+{
     DiagAcc acc;
-    e = cudaMemcpyAsync(&acc, h->acc, sizeof acc, cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(&acc, h->acc, sizeof acc, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: read back");
-    int st = check_device_flag(h, "elbm_diagnostics");
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    int st = check_device_flag(h, what);
     if (st != ELBM_OK) return st;
     const int64_t N = h->g.N;
     out->mass = acc.sum[0];
@@ -516,9 +517,57 @@ int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist)
     if (alpha_hist)
         for (int b = 0; b < ELBM_HIST_BINS + 2; ++b) alpha_hist[b] = int64_t(acc.hist[b]);
     if (out->n_nonpositive > 0)
-        return fail(h, ELBM_ERR_NONPHYSICAL, "elbm_diagnostics: %lld nodes with a population <= 0 or not finite",
+        return fail(h, ELBM_ERR_NONPHYSICAL, "%s: %lld nodes with a population <= 0 or not finite", what,
                     (long long)out->n_nonpositive);
     return ELBM_OK;
+}
+
+} // namespace
+
+int elbm_diagnostics(elbm_t *h, elbm_diag *out, int64_t *alpha_hist)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_diagnostics: handle is NULL");
+    if (!out) return fail(h, ELBM_ERR_ARG, "elbm_diagnostics: out is NULL");
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_diagnostics: no state");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = clear_diag_acc(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: clear scratch");
+    e = ELBM_BY_LATTICE(h, launch_diag, h->opts.storage, h->pop[h->cur], h->g, params_of(h), h->acc, h->num_sms,
+                        h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_diagnostics: kernel launch");
+    return read_diag_acc(h, out, alpha_hist, "elbm_diagnostics");
+}
+
+int elbm_step_diag(elbm_t *h, int64_t n, elbm_diag *out, int64_t *alpha_hist)
+{
+    if (!h) return fail(nullptr, ELBM_ERR_ARG, "elbm_step_diag: handle is NULL");
+    if (!out) return fail(h, ELBM_ERR_ARG, "elbm_step_diag: out is NULL");
+    if (n < 1) return fail(h, ELBM_ERR_ARG, "elbm_step_diag: n = %lld < 1", (long long)n);
+    if (!h->pop[0]) return fail(h, ELBM_ERR_ARG, "elbm_step_diag: no state");
+    DeviceGuard guard(h->opts.device);
+    cudaError_t e = clear_diag_acc(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_step_diag: clear scratch");
+    const CollideParams p = params_of(h);
+    int64_t done = 0;
+    if (h->opts.kernel != ELBM_KERNEL_ROWS) {
+        e = ELBM_BY_LATTICE(h, launch_step_diag, h->opts.storage, h->pop[h->cur], h->pop[h->cur ^ 1], h->g, p,
+                            h->acc, h->num_sms, h->stream);
+        if (e == cudaSuccess) {
+            h->cur ^= 1;
+            ++h->steps;
+            done = 1;
+        } else if (e != cudaErrorNotSupported) {
+            return cuda_fail(h, e, "elbm_step_diag: kernel launch");
+        }
+    }
+    if (!done) { // diagnostics pass, then the step (rows kernel, body force, very large domains)
+        e = ELBM_BY_LATTICE(h, launch_diag, h->opts.storage, h->pop[h->cur], h->g, p, h->acc, h->num_sms,
+                            h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_step_diag: kernel launch");
+    }
+    const int st = elbm_step(h, n - done);
+    if (st != ELBM_OK) return st;
+    return read_diag_acc(h, out, alpha_hist, "elbm_step_diag");
 }
 
 int elbm_get_populations(elbm_t *h, void *dst, int where)

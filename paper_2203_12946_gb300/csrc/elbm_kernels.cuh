@@ -236,47 +236,29 @@ __device__ __forceinline__ unsigned long long warp_min(unsigned long long v)
     return v;
 }
 
-template <class ST>
-__global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__restrict__ fin,
-                                                   Geometry g, CollideParams p,
-                                                   DiagAcc *__restrict__ acc)
-{
-    using T = typename ST::T;
-    constexpr int kWarps = kAuxBlock / 32;
-    __shared__ double s_sum[kWarps][6];
-    __shared__ unsigned long long s_cnt[kWarps][5];
-    __shared__ unsigned long long s_ext[kWarps][3];
-    __shared__ unsigned int s_hist[ELBM_HIST_BINS + 2];
-
-    for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kAuxBlock) s_hist[b] = 0u;
-    __syncthreads();
-
+// Per-thread accumulation of the domain diagnostics of a node and of the collision
+// it undergoes (used by k_diag and by the step fused with diagnostics).  Partial sums
+// in the compute type of the small parts (deviations, H + 1, alpha - 2) over the
+// thread's nodes; the exact parts (one per node, 2 per alpha) and the conversion to
+// FP64 are added once per thread in diag_finish (FP64 arithmetic is slow on this GPU,
+// and per node it was a third of the pass).
+template <class T>
+struct DiagThread {
     double sum[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long cnt[5] = {0, 0, 0, 0, 0};
     unsigned long long dmax = 0ULL, amin = ~0ULL, amax = 0ULL;
-    // Per-thread partial sums in the compute type of the small parts (deviations, H + 1,
-    // alpha - 2) over the thread's few dozen nodes; the exact parts (one per node, 2 per
-    // alpha) and the conversion to FP64 are added once per thread below (FP64 arithmetic
-    // is slow on this GPU, and per node it was a third of the kernel's work).
     T p_dr = T(0), p_j[3] = {T(0), T(0), T(0)}, p_h = T(0), p_al = T(0);
     T p_dmax = -INFINITY, p_amin = INFINITY, p_amax = -INFINITY;
     unsigned long long p_nodes = 0, p_hnodes = 0;
 
-    for (int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; n < g.N;
-         n += (int64_t)gridDim.x * kAuxBlock) {
-        int x, y, z;
-        node_coords(n, g, x, y, z);
-        T f[Q], xd[Q];
-        pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
-        T fc[Q];
+    // fc: the node's pre-collision populations; xd, alpha_t, br: departures, path length
+    // and branch of its collision; s_hist: the block's histogram in shared memory.
+    __device__ __forceinline__ void node(const T (&fc)[Q], const T (&xd)[Q], const T alpha_t, const int br,
+                                         const CollideParams &p, unsigned int *s_hist)
+    {
         bool bad = false;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            fc[i] = f[i];
-            bad |= !(f[i] > T(0)) || !isfinite(f[i]);
-        }
-        int br;
-        const T alpha_t = collide<D, T, false>(f, xd, p, &br);
+        for (int i = 0; i < Q; ++i) bad |= !(fc[i] > T(0)) || !isfinite(fc[i]);
 
         // Mass and momentum through the deviations d_i = f_i - w_i (small numbers).
         T dr = T(0), jt[3] = {T(0), T(0), T(0)};
@@ -363,6 +345,24 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         else bin = 1 + min(ELBM_HIST_BINS - 1, int(off * T(ELBM_HIST_BINS / 0.2)));
         atomicAdd(&s_hist[bin], 1u);
     }
+};
+
+// Block reduction of the per-thread diagnostics into the FP64 accumulator (warp
+// shuffles, then shared memory, then one atomic per block and quantity).  NT >= 65.
+template <int NT, class T>
+__device__ __forceinline__ void diag_finish(DiagThread<T> &dt, DiagAcc *__restrict__ acc, unsigned int *s_hist)
+{
+    constexpr int kWarps = NT / 32;
+    __shared__ double s_sum[kWarps][6];
+    __shared__ unsigned long long s_cnt[kWarps][5];
+    __shared__ unsigned long long s_ext[kWarps][3];
+    double (&sum)[6] = dt.sum;
+    unsigned long long (&cnt)[5] = dt.cnt;
+    unsigned long long &dmax = dt.dmax, &amin = dt.amin, &amax = dt.amax;
+    const T &p_dr = dt.p_dr, &p_h = dt.p_h, &p_al = dt.p_al;
+    const T(&p_j)[3] = dt.p_j;
+    const T &p_dmax = dt.p_dmax, &p_amin = dt.p_amin, &p_amax = dt.p_amax;
+    const unsigned long long p_nodes = dt.p_nodes, p_hnodes = dt.p_hnodes;
     // this thread's nodes into the FP64 sums: mass = sum (1 + e_w + dr), H = sum hl - rho
     {
         const double nn = double(p_nodes), one = 1.0 + weight_sum_error<D, T>();
@@ -413,8 +413,79 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         atomicMin(&acc->amin_ord, b);
         atomicMax(&acc->amax_ord, c);
     }
-    for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kAuxBlock)
+    for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += NT)
         if (s_hist[b]) atomicAdd(&acc->hist[b], (unsigned long long)s_hist[b]);
+}
+
+template <class ST>
+__global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__restrict__ fin,
+                                                   Geometry g, CollideParams p,
+                                                   DiagAcc *__restrict__ acc)
+{
+    using T = typename ST::T;
+    __shared__ unsigned int s_hist[ELBM_HIST_BINS + 2];
+    for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kAuxBlock) s_hist[b] = 0u;
+    __syncthreads();
+    DiagThread<T> dt;
+    for (int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; n < g.N;
+         n += (int64_t)gridDim.x * kAuxBlock) {
+        int x, y, z;
+        node_coords(n, g, x, y, z);
+        T f[Q], xd[Q], fc[Q];
+        pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fc[i] = f[i];
+        int br;
+        const T alpha_t = collide<D, T, false>(f, xd, p, &br);
+        dt.node(fc, xd, alpha_t, br, p, s_hist);
+    }
+    diag_finish<kAuxBlock>(dt, acc, s_hist);
+}
+
+// The step fused with the diagnostics of the state it advances (the quantities of
+// k_diag, taken from the collision the step performs): 3D-grid addressing with 32-bit
+// offsets, one node per thread, a grid of a few blocks per SM looping over the
+// (x-block, y, z) items so that each block reduces and posts its sums once.
+template <class ST>
+__global__ void ELBM_STEP_BOUNDS k_step_diag(const typename ST::S *__restrict__ fin,
+                                             typename ST::S *__restrict__ fout, Geometry g, CollideParams p,
+                                             DiagAcc *__restrict__ acc)
+{
+    using T = typename ST::T;
+    __shared__ unsigned int s_hist[ELBM_HIST_BINS + 2];
+    for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kStepBlock) s_hist[b] = 0u;
+    __syncthreads();
+    DiagThread<T> dt;
+    const T rho0 = T(p.rho0);
+    const uint32_t nx = uint32_t(g.nx), ny = uint32_t(g.ny), nz = uint32_t(g.nz), N = uint32_t(g.N);
+    const uint32_t xblocks = (nx + kStepBlock - 1) / kStepBlock;
+    const uint32_t items = xblocks * ny * nz;
+    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const uint32_t xb = it % xblocks, yz = it / xblocks;
+        const uint32_t y = yz % ny, z = yz / ny;
+        const uint32_t x = xb * kStepBlock + threadIdx.x;
+        if (x >= nx) continue;
+        const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        T f[Q], xd[Q], fc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+            const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+            const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+            const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+            f[i] = ST::load(__ldg(fin + (uint32_t(i) * N + (sz * ny + sy) * nx + sx)), T(weight(D, i)), rho0);
+            fc[i] = f[i];
+        }
+        int br;
+        const T alpha_t = collide<D, T, true>(f, xd, p, &br);
+        dt.node(fc, xd, alpha_t, br, p, s_hist);
+        const uint32_t n = (z * ny + y) * nx + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::store(f[i], T(weight(D, i)), rho0));
+    }
+    diag_finish<kStepBlock>(dt, acc, s_hist);
 }
 
 // --------------------------------------------------------------------------
@@ -715,6 +786,23 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
                                              static_cast<typename ST::S *>(fout), g, p)));
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(launch_step_diag, ELBM_SUFFIX)(int storage, const void *fin, void *fout, const Geometry &g,
+                                                    const CollideParams &p, DiagAcc *acc, int num_sms,
+                                                    cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (g.N == 0) return cudaSuccess;
+    const bool forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
+    if (forced || uint64_t(Q) * uint64_t(g.N) > 0xffffffffull) return cudaErrorNotSupported;
+    const uint64_t items = uint64_t((g.nx + kStepBlock - 1) / kStepBlock) * uint64_t(g.ny) * uint64_t(g.nz);
+    const uint64_t cap = uint64_t(num_sms > 0 ? num_sms : 1) * 8u;
+    const unsigned grid = unsigned(items < cap ? items : cap);
+    ELBM_STORAGE_SWITCH(storage, (k_step_diag<ST><<<grid, kStepBlock, 0, s>>>(
+                                     static_cast<const typename ST::S *>(fin), static_cast<typename ST::S *>(fout),
+                                     g, p, acc)));
     return cudaGetLastError();
 }
 

@@ -64,6 +64,9 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
     cudaError_t launch_diag_##SUFFIX(int storage, const void *f, const Geometry &g,                 \
                                      const CollideParams &p, DiagAcc *acc, int num_sms,             \
                                      cudaStream_t s);                                                \
+    cudaError_t launch_step_diag_##SUFFIX(int storage, const void *fin, void *fout, const Geometry &g,    \
+                                          const CollideParams &p, DiagAcc *acc, int num_sms,            \
+                                          cudaStream_t s);                                              \
     cudaError_t launch_step_batch_##SUFFIX(int storage, const void *fin, void *fout,                \
                                            const BatchDomain *doms, const int4 *items, int nitems,   \
                                            int bx, const CollideParams &p, cudaStream_t s);          \

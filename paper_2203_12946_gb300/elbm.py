@@ -51,7 +51,7 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
             "elbm_batch_init_equilibrium", "elbm_batch_step", "elbm_batch_tune", "elbm_batch_moments",
             "elbm_batch_diagnostics", "elbm_batch_get_populations", "elbm_batch_set_populations",
             "elbm_batch_synchronize", "elbm_adjoint_step", "elbm_kinetic_energy", "elbm_equilibrium_vjp",
-            "elbm_subgrid_viscosity", "elbm_adjoint_step_force", "elbm_set_force"]
+            "elbm_subgrid_viscosity", "elbm_adjoint_step_force", "elbm_set_force", "elbm_step_diag"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -144,6 +144,7 @@ def load(build_if_missing: bool = True):
             "elbm_subgrid_viscosity": (ctypes.c_int, [P, P, ctypes.c_int]),
             "elbm_adjoint_step_force": (ctypes.c_int, [P, P, P, P, P]),
             "elbm_set_force": (ctypes.c_int, [P, P]),
+            "elbm_step_diag": (ctypes.c_int, [P, ctypes.c_int64, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -245,6 +246,17 @@ def elbm_diagnostics(h, alpha_hist: np.ndarray | None = None, allow_nonphysical:
     code = load().elbm_diagnostics(h, ctypes.byref(d), _ptr(alpha_hist))
     if not (allow_nonphysical and code == ELBM_ERR_NONPHYSICAL):
         _check(h, code, "elbm_diagnostics")
+    out = d.as_dict()
+    out["status"] = code
+    return out
+
+
+def elbm_step_diag(h, n: int, alpha_hist: np.ndarray | None = None, allow_nonphysical: bool = False) -> dict:
+    """n steps, the first taking the diagnostics of the state before them."""
+    d = elbm_diag()
+    code = load().elbm_step_diag(h, int(n), ctypes.byref(d), _ptr(alpha_hist))
+    if not (allow_nonphysical and code == ELBM_ERR_NONPHYSICAL):
+        _check(h, code, "elbm_step_diag")
     out = d.as_dict()
     out["status"] = code
     return out
@@ -408,6 +420,14 @@ class Simulation:
         nut = self.torch.empty(self.N, dtype=self.torch.float64, device=self.device)
         elbm_subgrid_viscosity(self.h, nut, ELBM_MEM_DEVICE)
         return nut
+
+    def step_diag(self, n, with_hist=False, allow_nonphysical=False):
+        """n steps; returns the diagnostics of the state before them (one fused pass)."""
+        hist = np.zeros(ELBM_HIST_BINS + 2, dtype=np.int64) if with_hist else None
+        d = elbm_step_diag(self.h, n, hist, allow_nonphysical)
+        if with_hist:
+            d["alpha_hist"] = hist
+        return d
 
     def diagnostics(self, with_hist=False, allow_nonphysical=False):
         hist = np.zeros(ELBM_HIST_BINS + 2, dtype=np.int64) if with_hist else None

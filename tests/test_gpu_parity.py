@@ -412,6 +412,45 @@ def test_diagnostics_against_oracle():
     assert np.sum(np.abs(hist[1:-1] - inner)) <= 4
 
 
+@pytest.mark.parametrize("D,dims,storage,kernel,force", [
+    (2, (77, 41, 1), "f32", E.ELBM_KERNEL_DIRECT, False),
+    (3, (23, 19, 11), "f32", E.ELBM_KERNEL_DIRECT, False),
+    (3, (23, 19, 11), "f64", E.ELBM_KERNEL_DIRECT, False),
+    (2, (64, 40, 1), "f32", E.ELBM_KERNEL_ROWS, False),   # diagnostics pass, then the step
+    (2, (61, 33, 1), "f32", E.ELBM_KERNEL_DIRECT, True),  # body force: diagnostics pass first
+])
+def test_step_diag_equals_diagnostics_then_steps(D, dims, storage, kernel, force):
+    """elbm_step_diag(n) reports what elbm_diagnostics reports before elbm_step(n), and
+    leaves the same state; called twice in a row."""
+    beta = 0.993
+    f0 = noisy_state(D, dims, 4e-3, seed=47)
+    if storage == "f32":
+        f0 = f0.astype(np.float32)
+    F = np.array([1e-4, -2e-4, 5e-5])[:D] if force else None
+    with E.Simulation(LAT[D], dims, beta, storage=storage, kernel=kernel) as a, \
+            E.Simulation(LAT[D], dims, beta, storage=storage, kernel=kernel) as b:
+        for sim in (a, b):
+            sim.set_populations(f0)
+            sim.set_force(F)
+        for n in (3, 1):
+            want = a.diagnostics(with_hist=True)
+            a.step(n)
+            got = b.step_diag(n, with_hist=True)
+            fa = a.get_populations().astype(np.float64)
+            fb = b.get_populations().astype(np.float64)
+            assert np.max(np.abs(fa - fb) / np.abs(fa)) < (1e-14 if storage == "f64" else 1e-6)
+            for k in ("n_nodes", "n_cutoff", "n_solved", "n_clamped", "n_nonpositive", "n_dH_positive"):
+                assert got[k] == want[k], k
+            assert np.array_equal(got["alpha_hist"], want["alpha_hist"])
+            rel = 1e-12 if storage == "f64" else 1e-6
+            assert abs(got["mass"] - want["mass"]) <= rel * want["mass"]
+            assert abs(got["H"] - want["H"]) <= rel * abs(want["H"])
+            assert np.allclose(got["momentum"], want["momentum"], rtol=0, atol=rel * want["mass"])
+            for k in ("alpha_min", "alpha_max", "alpha_mean", "dH_max"):
+                assert abs(got[k] - want[k]) <= rel * 2.0 + 1e-15, k
+            assert a.steps == b.steps
+
+
 def test_nonphysical_state_is_reported():
     D, dims = 2, (16, 8, 1)
     f0 = noisy_state(D, dims, 1e-3)
