@@ -741,7 +741,7 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
     if (g.N == 0) return cudaSuccess;
     const bool forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
     // AUTO takes DIRECT: on GB300 it is the faster of the two at every size measured
-    // (D3Q27 256^3 FP32: 0.83 ms against 0.94 ms for ROWS).  The body force runs on DIRECT only.
+    // (D3Q27 256^3 FP32: 0.63 ms against 0.70 ms for ROWS).  The body force runs on DIRECT only.
     if (kernel == ELBM_KERNEL_ROWS && forced) return cudaErrorNotSupported;
     if (kernel == ELBM_KERNEL_ROWS && ELBM_CAT(rows_kernel_applies, ELBM_SUFFIX)(storage, g)) {
         // the row pipeline is only instantiated for the FP32 and 16-bit storages
