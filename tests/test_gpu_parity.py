@@ -602,3 +602,36 @@ def test_rows_kernel_rejected_where_it_does_not_apply(D, dims, storage):
     with pytest.raises(E.ElbmError) as ei:
         E.Simulation(LAT[D], dims, 0.9, storage=storage, kernel=E.ELBM_KERNEL_ROWS)
     assert ei.value.code == E.ELBM_ERR_UNSUPPORTED
+
+
+def test_error_paths_of_the_force_and_fused_diagnostics_calls():
+    """Invalid arguments come back as status codes with a message, and leave the handle usable."""
+    import torch
+
+    D, dims = 2, (64, 16, 1)
+    f0 = noisy_state(D, dims, 1e-3, seed=53)
+    with E.Simulation(E.ELBM_D2Q9, dims, 0.95, storage="f32", kernel=E.ELBM_KERNEL_ROWS) as sim:
+        sim.set_populations(f0.astype(np.float32))
+        with pytest.raises(E.ElbmError) as ei:
+            sim.set_force([1e-4, 0.0])  # the body force runs on the DIRECT kernel only
+        assert ei.value.code == E.ELBM_ERR_UNSUPPORTED
+        sim.set_force(None)  # no force: accepted
+        sim.step(1)
+    with E.Simulation(E.ELBM_D2Q9, dims, 0.95, storage="f32") as sim:
+        sim.set_populations(f0.astype(np.float32))
+        with pytest.raises(E.ElbmError) as ei:
+            sim.set_force([np.nan, 0.0])
+        assert ei.value.code == E.ELBM_ERR_ARG
+        with pytest.raises(E.ElbmError) as ei:
+            sim.step_diag(0)
+        assert ei.value.code == E.ELBM_ERR_ARG
+        g = torch.zeros((9, sim.N), dtype=torch.float32, device="cuda")
+        with pytest.raises(E.ElbmError) as ei:
+            E.elbm_adjoint_step_force(sim.h, sim.state_copy(), g, torch.empty_like(g), None)
+        assert ei.value.code == E.ELBM_ERR_ARG
+        with pytest.raises(E.ElbmError) as ei:
+            E.elbm_adjoint_step_force(sim.h, sim.state_copy(), g, g,
+                                      torch.zeros(2, dtype=torch.float64, device="cuda"))
+        assert ei.value.code == E.ELBM_ERR_ARG  # g_t aliases g_next
+        d = sim.step_diag(2)  # the handle still works
+        assert d["n_nodes"] == sim.N and sim.steps == 2
