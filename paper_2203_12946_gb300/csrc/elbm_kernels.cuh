@@ -302,7 +302,7 @@ struct DiagThread {
                 T abk = ab * ab; // ab^(k-1) at k = 3
 #pragma unroll
                 for (int k = 3; k <= kTop; ++k) {
-                    const T v = ab / T(k - 1) * (abk / T(k) - T(1));
+                    const T v = ab * T(1.0 / (k - 1)) * (abk * T(1.0 / k) - T(1));
                     ck[k] = (k & 1) ? -v : v;
                     abk *= ab;
                 }
@@ -446,8 +446,15 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
 // k_diag, taken from the collision the step performs): 3D-grid addressing with 32-bit
 // offsets, one node per thread, a grid of a few blocks per SM looping over the
 // (x-block, y, z) items so that each block reduces and posts its sums once.
+// Its own register budget: the diagnostics' extra live values spilled heavily under
+// the step's 72-register cap (3 blocks of 128 for D3Q27, 2 of 256 for D2Q9; FP64 unbounded).
 template <class ST>
-__global__ void ELBM_STEP_BOUNDS k_step_diag(const typename ST::S *__restrict__ fin,
+constexpr int step_diag_min_blocks()
+{
+    return sizeof(typename ST::T) != 4 ? 1 : (D == 3 ? 3 : 2);
+}
+template <class ST>
+__global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step_diag(const typename ST::S *__restrict__ fin,
                                              typename ST::S *__restrict__ fout, Geometry g, CollideParams p,
                                              DiagAcc *__restrict__ acc)
 {
