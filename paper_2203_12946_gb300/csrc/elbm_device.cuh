@@ -546,12 +546,36 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         //       = 1 - x/2 + x^2/3 - x^3/4 + x^4/5 - ...      (c; log(1+x)/x to x^5)
         //   2/(4+t) + 1/(4+2t) + 2/(4+3t) = 5/4 - 5t/8 + 3t^2/8 - t^3/4 + ...   (b, t = k x)
         // with the Omega+ sums P_m = M_m - S_m.  Kept to M6: at |x| = 0.02 the dropped
-        // terms are ~1e-10 of c1 and c and ~4e-9 of b.  The series form needs no
-        // reciprocal per population and no second pass for b.
-        constexpr float kSeriesX = 0.02f;
+        // terms are ~1e-10 of c1 and c and ~4e-9 of b.  Where |x|max < kShortX the
+        // series stop at x^4 (M2..M4, S3, S4): the dropped terms are bounded by
+        // |x|max^3 = 1.25e-7 of M2 times their coefficients (1/8 in c1, 1/4 in c), and
+        // alpha moves by at most ~3e-8 relative, below FP32 rounding.  The series forms
+        // need no reciprocal per population and no second pass for b.
+        constexpr float kSeriesX = 0.02f, kShortX = 0.005f;
         const bool series = xabs < kSeriesX;
-        float sb1, sc1, sc, s3, s4, s5, s6, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f, m6 = 0.0f;
-        if (series) {
+        float sb1, sc1, sc, s3, s4, s5 = 0.0f, s6 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f, m6 = 0.0f;
+        if (xabs < kShortX) {
+            float2 M2 = f2(0.0f), M3 = f2(0.0f), M4 = f2(0.0f), S3 = f2(0.0f), S4 = f2(0.0f);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float2 xi = xp[k];
+                const float2 fx2 = pmul(fp[k], pmul(xi, xi)); // f x^2
+                const float2 q3 = pmul(fx2, xi);
+                M2 = padd(M2, fx2);
+                M3 = padd(M3, q3);
+                M4 = pfma(q3, xi, M4);
+                const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+                const float2 q = pmul(fx2, xm); // f x^3 on Omega-, 0 elsewhere
+                S3 = padd(S3, q);
+                S4 = pfma(q, xm, S4);
+            }
+            const float m2 = M2.x + M2.y;
+            m3 = M3.x + M3.y, m4 = M4.x + M4.y;
+            sb1 = 0.5f * m2;
+            sc1 = m2 + (m3 * -0.5f + m4 * 0.25f);
+            sc = m2 + (m3 * -0.5f + m4 * (1.0f / 3.0f));
+            s3 = S3.x + S3.y, s4 = S4.x + S4.y;
+        } else if (series) {
             float2 M2 = f2(0.0f), M3 = f2(0.0f), M4 = f2(0.0f), M5 = f2(0.0f), M6 = f2(0.0f);
             float2 S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
 #pragma unroll
