@@ -411,12 +411,16 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
 // FP32 collision on packed population pairs.
 //
 // The same arithmetic as node_collide<D, float>, evaluated on float2 pairs of
-// populations (2k, 2k+1) with the sm_100-family paired FP32 instructions
-// (__ffma2_rn, __fmul2_rn, __fadd2_rn: two IEEE FP32 operations per
-// instruction).  With Q odd the last pair carries a padding lane (f = 1,
-// x = 0) that contributes nothing to any sum.  The Omega-/Omega+ restricted
-// sums are taken branch-free with min(x,0) / max(x,0): a term of the other set
-// is exactly zero, so the sums equal the restricted ones.
+// populations with the sm_100-family paired FP32 instructions (__ffma2_rn,
+// __fmul2_rn, __fadd2_rn: two IEEE FP32 operations per instruction).  The two
+// populations of a pair have velocities that mirror each other along one axis m
+// (lane 0: c_m = -1, lane 1: c_m = +1) and agree on the other axes, so both lanes
+// share the weight and the other axes' equilibrium factors: first the Q/3 pairs
+// mirrored along the last axis, then, among the populations at rest along it, those
+// mirrored along the axis before, and so on; the rest population comes last with a
+// padding lane (f = 1, x = 0) that contributes nothing to any sum.  The
+// Omega-/Omega+ restricted sums are taken branch-free with min(x,0) / max(x,0): a
+// term of the other set is exactly zero, so the sums equal the restricted ones.
 //   in : fp[NP]  pre-collision populations, pair layout
 //   out: fp[NP]  post-collision populations (when kRelax)
 //        xp[NP]  departures x_i (Eq. xdef), pair layout
@@ -428,6 +432,34 @@ struct Pairs {
     static constexpr int NP = (Q + 1) / 2;
 };
 
+// Population held by lane `lane` of pair k (-1: the padding lane), lexicographic
+// population order i = sum_a 3^(D-1-a) (c_a + 1).
+__host__ __device__ constexpr int pair_pop(int D, int k, int lane)
+{
+    if (D == 3) {
+        if (k < 9) return 3 * k + 2 * lane;            // (c_x, c_y) from k; c_z = -1, +1
+        if (k < 12) return 9 * (k - 9) + 1 + 6 * lane; // c_x = k - 10; c_y = -1, +1; c_z = 0
+        if (k == 12) return 4 + 18 * lane;             // c_x = -1, +1; c_y = c_z = 0
+        return lane ? -1 : 13;                         // rest
+    }
+    if (k < 3) return 3 * k + 2 * lane; // c_x = k - 1; c_y = -1, +1
+    if (k == 3) return 1 + 6 * lane;    // c_x = -1, +1; c_y = 0
+    return lane ? -1 : 4;               // rest
+}
+// Mirrored axis of pair k (-1 for the rest pair).
+__host__ __device__ constexpr int pair_axis(int D, int k)
+{
+    return D == 3 ? (k < 9 ? 2 : k < 12 ? 1 : k == 12 ? 0 : -1) : (k < 3 ? 1 : k == 3 ? 0 : -1);
+}
+// Slot 2 k + lane that holds population i.
+__host__ __device__ constexpr int pair_slot(int D, int i)
+{
+    for (int k = 0; k < (Lattice<3>::Q + 1) / 2; ++k)
+        for (int lane = 0; lane < 2; ++lane)
+            if (pair_pop(D, k, lane) == i) return 2 * k + lane;
+    return -1;
+}
+
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -436,16 +468,16 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
 __device__ __forceinline__ float2 prcp(float2 a) { return f2(rcp_(a.x), rcp_(a.y)); }
 
-// Weight pair of pair k, as k_i T(W) (0 in the padding lane), and the k_i pair.
+// Weight of pair k's lane, as k_i T(W) (0 in the padding lane), and its k_i.
 template <int D>
 __host__ __device__ constexpr float wpair(int k, int lane)
 {
-    return (2 * k + lane) < Lattice<D>::Q ? float(weight_k(D, 2 * k + lane)) * float(weight_unit(D)) : 0.0f;
+    return pair_pop(D, k, lane) >= 0 ? float(weight_k(D, pair_pop(D, k, lane))) * float(weight_unit(D)) : 0.0f;
 }
 template <int D>
 __host__ __device__ constexpr float kpair(int k, int lane)
 {
-    return (2 * k + lane) < Lattice<D>::Q ? float(weight_k(D, 2 * k + lane)) : 0.0f;
+    return pair_pop(D, k, lane) >= 0 ? float(weight_k(D, pair_pop(D, k, lane))) : 0.0f;
 }
 
 template <int D, bool kRelax = true>
@@ -462,7 +494,10 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
     float2 dp[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) dp[k] = psub(fp[k], f2(wpair<D>(k, 0), wpair<D>(k, 1)));
-    auto ds = [&](int i) -> float { return (i & 1) ? dp[i >> 1].y : dp[i >> 1].x; };
+    auto ds = [&](int i) -> float {
+        const int sl = pair_slot(D, i);
+        return (sl & 1) ? dp[sl >> 1].y : dp[sl >> 1].x;
+    };
     constexpr int P = Q / 3;
     float s0[P], s1[P];
 #pragma unroll
@@ -504,18 +539,23 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         eps[a][1] = -t;
         eps[a][2] = 2.0f * t + 3.0f * u;
     }
-    // E_i = prod_a (1 + eps_a(c_ia)) - 1, per population.
-    auto E_of = [&](int i) -> float {
-        if (i >= Q) return 0.0f;
-        float A;
-        if (D == 2) {
-            A = eps[0][i / 3];
-        } else {
-            const float ex = eps[0][i / 9], ey = eps[1][(i / 3) % 3];
-            A = ex + ey + ex * ey;
+    // E_i = prod_a (1 + eps_a(c_ia)) - 1 per pair: G = prod over the axes other than the
+    // mirrored one m, minus 1 (shared by both lanes), then E = G + e + G e with
+    // e = (eps_m(-1), eps_m(+1)).
+    auto E_pair = [&](int k) -> float2 {
+        const int m = pair_axis(D, k), i0 = pair_pop(D, k, 0);
+        float G = 0.0f;
+        bool first = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            if (a == m) continue;
+            const float e = eps[a][vel(D, i0, a) + 1];
+            G = first ? e : G + e + G * e;
+            first = false;
         }
-        const float el = eps[D - 1][i % 3];
-        return A + el + A * el;
+        if (m < 0) return f2(G, 0.0f);
+        const float2 em = f2(eps[m][0], eps[m][2]);
+        return pfma(f2(G), em, padd(f2(G), em));
     };
 
     // x_i = (f^eq_i - f_i) / f_i and its extremes; the sums of the path length are
@@ -523,7 +563,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
     float xabs = 0.0f, xmin = 0.0f;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        const float2 E = f2(E_of(2 * k), E_of(2 * k + 1));
+        const float2 E = E_pair(k);
         // f^eq - f = (k_i r) E_i + (k_i r - f_i), one rounding (as in node_collide)
         const float2 kr = pmul(f2(kpair<D>(k, 0), kpair<D>(k, 1)), f2(r));
         float2 delta = pfma(kr, E, psub(kr, fp[k]));
@@ -694,12 +734,16 @@ __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q
         constexpr int NP = Pairs<D>::NP;
         float2 fp[NP], xp[NP];
 #pragma unroll
-        for (int k = 0; k < NP; ++k) fp[k] = make_float2(f[2 * k], (2 * k + 1 < Q) ? f[2 * k + 1] : 1.0f);
+        for (int k = 0; k < NP; ++k) {
+            const int i1 = pair_pop(D, k, 1);
+            fp[k] = make_float2(f[pair_pop(D, k, 0)], i1 >= 0 ? f[i1] : 1.0f);
+        }
         const float alpha = node_collide_pairs<D, kRelax>(fp, xp, p, branch);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            x[i] = (i & 1) ? xp[i >> 1].y : xp[i >> 1].x;
-            if (kRelax) f[i] = (i & 1) ? fp[i >> 1].y : fp[i >> 1].x;
+            const int sl = pair_slot(D, i);
+            x[i] = (sl & 1) ? xp[sl >> 1].y : xp[sl >> 1].x;
+            if (kRelax) f[i] = (sl & 1) ? fp[sl >> 1].y : fp[sl >> 1].x;
         }
         return alpha;
     } else {
