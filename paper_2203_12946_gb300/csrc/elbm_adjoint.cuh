@@ -43,7 +43,7 @@ __device__ void node_vjp(const T (&F)[Lattice<D>::Q], const T (&gin0)[Lattice<D>
                          T (&h)[Lattice<D>::Q], T *dforce = nullptr)
 {
     constexpr int Q = Lattice<D>::Q;
-    const T beta = T(p.beta);
+    const T beta = beta_of<T>(p);
 
     // ---- forward: moments and the equilibrium (Sec. I), in the forms the step uses ----
     // Deviations from k_i T(W) (exact), drho corrected for the rest of W, r = rho W in two

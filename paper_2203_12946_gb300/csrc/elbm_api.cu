@@ -78,6 +78,8 @@ CollideParams params_of(const elbm_t *h)
     p.cutoff = h->opts.cutoff;
     p.b_variant = h->opts.b_variant;
     p.rho0 = h->opts.rho0;
+    p.beta_f = float(p.beta);
+    p.rho0_f = float(p.rho0);
     for (int a = 0; a < 3; ++a) p.force[a] = h->force[a];
     return p;
 }

@@ -93,6 +93,8 @@ CollideParams params_of(const elbm_batch_t *b, double beta)
     p.cutoff = b->opts.cutoff;
     p.b_variant = b->opts.b_variant;
     p.rho0 = b->opts.rho0;
+    p.beta_f = float(p.beta);
+    p.rho0_f = float(p.rho0);
     return p;
 }
 
@@ -225,10 +227,10 @@ int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64
         m.nx = int(dd[0]);
         m.ny = int(dd[1]);
         m.nz = int(dd[2]);
-        m.pad = 0;
         m.N = dd[0] * dd[1] * dd[2];
         m.off = int64_t(total);
         m.beta = beta[d];
+        m.beta_f = float(beta[d]);
         total += (size_t(Q) * size_t(m.N) + align - 1) / align * align;
     }
     int ndev = 0;

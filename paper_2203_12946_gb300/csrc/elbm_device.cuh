@@ -83,7 +83,23 @@ struct CollideParams {
     int b_variant; // 0 = derived denominators (alpha_L beta x), 1 = printed (alpha_L x)
     double rho0;   // reference density of deviation storage
     double force[3] = {0.0, 0.0, 0.0}; // uniform body force (not from the paper), used by the forced kernels
+    float beta_f = 0.0f; // beta and rho0 rounded to FP32 once on the host (the FP32 kernels
+    float rho0_f = 0.0f; // read these and convert nothing from FP64 per thread)
 };
+
+// beta and rho0 in the compute type.
+template <class T>
+__device__ __forceinline__ T beta_of(const CollideParams &p)
+{
+    if constexpr (sizeof(T) == 4) return p.beta_f;
+    else return p.beta;
+}
+template <class T>
+__device__ __forceinline__ T rho0_of(const CollideParams &p)
+{
+    if constexpr (sizeof(T) == 4) return p.rho0_f;
+    else return p.rho0;
+}
 
 // ---------------------------------------------------------------------------
 // Arithmetic helpers.  FP32 divisions on the hot path multiply by the
@@ -228,7 +244,7 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
                                           const CollideParams &p, int *branch)
 {
     constexpr int Q = Lattice<D>::Q;
-    const T beta = T(p.beta);
+    const T beta = beta_of<T>(p);
 
     // Deviations from the weights and the moments (Sec. I): rho = <f,1>,
     // rho u = <f,c> = <d,c> (the weights carry no momentum).  Sums are taken
@@ -487,7 +503,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
     constexpr int Q = Lattice<D>::Q;
     constexpr int NP = Pairs<D>::NP;
     constexpr bool kPad = (Q % 2) == 1;
-    const float beta = float(p.beta);
+    const float beta = p.beta_f;
 
     // Deviations d_i = f_i - w_i and the moments (Sec. I), summed along the last
     // axis first (same grouping as node_collide).

@@ -78,7 +78,7 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
 {
     using T = typename ST::T;
     T f[Q], xd[Q];
-    const T rho0 = T(p.rho0);
+    const T rho0 = rho0_of<T>(p);
     int br;
     if constexpr (kGrid3D) {
         // 3D grid with Q N < 2^32: element offsets in 32 bits (the source rows of
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kStepBlock) k_alpha(const typename ST::S *__re
     int x, y, z;
     node_coords(n, g, x, y, z);
     T f[Q], xd[Q];
-    pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
+    pull_load<D, ST>(fin, g, x, y, z, rho0_of<T>(p), f);
     int br;
     const T alpha = collide<D, T, false>(f, xd, p, &br);
     if (alpha_out) alpha_out[n] = double(alpha);
@@ -280,7 +280,7 @@ struct DiagThread {
             // removing alpha beta <f,x> from both sums):
             // H[f*] - H[f] = <f, g(ab x)> - ab <f, x log(1+x)>, g(y) = (1+y) log(1+y) - y.
             // Per-node sums in the path's compute type, domain sums in FP64.
-            const T ab = alpha_t * T(p.beta);
+            const T ab = alpha_t * beta_of<T>(p);
             T hl = T(0), s3 = T(0), xa = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -298,7 +298,7 @@ struct DiagThread {
                 // form cancel to that small leading coefficient instead.
                 constexpr int kTop = 13;
                 T ck[kTop + 1];
-                ck[2] = T(0.5) * ab * fma(alpha_t, T(p.beta), T(-2));
+                ck[2] = T(0.5) * ab * fma(alpha_t, beta_of<T>(p), T(-2));
                 T abk = ab * ab; // ab^(k-1) at k = 3
 #pragma unroll
                 for (int k = 3; k <= kTop; ++k) {
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         int x, y, z;
         node_coords(n, g, x, y, z);
         T f[Q], xd[Q], fc[Q];
-        pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), f);
+        pull_load<D, ST>(fin, g, x, y, z, rho0_of<T>(p), f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) fc[i] = f[i];
         int br;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
     for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kStepBlock) s_hist[b] = 0u;
     __syncthreads();
     DiagThread<T> dt;
-    const T rho0 = T(p.rho0);
+    const T rho0 = rho0_of<T>(p);
     const uint32_t nx = uint32_t(g.nx), ny = uint32_t(g.ny), nz = uint32_t(g.nz), N = uint32_t(g.N);
     const uint32_t xblocks = (nx + kStepBlock - 1) / kStepBlock;
     const uint32_t items = xblocks * ny * nz;
@@ -514,9 +514,10 @@ __global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restr
     if (x >= dm.nx) return;
     const Geometry g{dm.nx, dm.ny, dm.nz, dm.N};
     p.beta = dm.beta;
+    p.beta_f = dm.beta_f;
     const int64_t n = ((int64_t)it.z * dm.ny + it.y) * dm.nx + x;
     T f[Q], xd[Q];
-    const T rho0 = T(p.rho0);
+    const T rho0 = rho0_of<T>(p);
     pull_load<D, ST>(fin + dm.off, g, x, it.y, it.z, rho0, f);
     int br;
     collide<D, T, true>(f, xd, p, &br);
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_step_adjoint(const typename ST::S
         int x, y, z;
         node_coords(n, g, x, y, z);
         T F[Q], gl[Q], h[Q];
-        pull_load<D, ST>(fin, g, x, y, z, T(p.rho0), F);
+        pull_load<D, ST>(fin, g, x, y, z, rho0_of<T>(p), F);
 #pragma unroll
         for (int i = 0; i < Q; ++i) gl[i] = gnext[(int64_t)i * g.N + n];
         node_vjp<D, T, kForce>(F, gl, p, h, dfl);

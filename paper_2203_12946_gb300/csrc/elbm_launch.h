@@ -16,7 +16,8 @@ struct CollideParams;
 // One domain of a batched ensemble: its own periodic box, populations at
 // element offset `off` of the shared buffers (SoA [Q][N] inside), and beta.
 struct BatchDomain {
-    int nx, ny, nz, pad;
+    int nx, ny, nz;
+    float beta_f; // beta rounded to FP32 on the host
     int64_t N;
     int64_t off;
     double beta;

@@ -146,6 +146,8 @@ extern "C" int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], doub
     p.cutoff = o.cutoff;
     p.b_variant = o.b_variant;
     p.rho0 = o.rho0;
+    p.beta_f = float(p.beta);
+    p.rho0_f = float(p.rho0);
     e = lattice == ELBM_D2Q9 ? eelbm::launch_diag_d2q9(o.storage, populations, g, p, acc, setup.num_sms, stream)
                              : eelbm::launch_diag_d3q27(o.storage, populations, g, p, acc, setup.num_sms, stream);
     if (e != cudaSuccess)

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
     const int G = gridDim.x;
     if (int(blockIdx.x) >= rows) return; // uniform over the CTA
     const uint32_t row_bytes = uint32_t(g.nx) * uint32_t(sizeof(S));
-    const T rho0 = T(p.rho0);
+    const T rho0 = rho0_of<T>(p);
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
