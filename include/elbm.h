@@ -317,14 +317,24 @@ typedef struct elbm_batch elbm_batch_t;
  * work items of every domain, the n launches captured once (per n and buffer
  * parity) into a CUDA graph that is replayed; LAUNCHES: the same launches
  * issued one by one; PER_DOMAIN: one single-domain launch per domain and step
- * (the baseline the batched forms are measured against). */
+ * (the baseline the batched forms are measured against); PERSISTENT: one
+ * cooperative launch advances every domain by n steps (up to 2^20 steps per
+ * launch), captured into a CUDA graph like GRAPH.  Its blocks, one per resident
+ * slot, own fixed runs of work items and wait only for the other owners of the
+ * same domain between steps; those waits are bounded (1 s), and one that
+ * expires leaves the steps incomplete and makes the next elbm_batch_synchronize
+ * return ELBM_ERR_TIMEOUT. */
 #define ELBM_BATCH_GRAPH 0
 #define ELBM_BATCH_LAUNCHES 1
 #define ELBM_BATCH_PER_DOMAIN 2
+#define ELBM_BATCH_PERSISTENT 3
 
 /* ndomains >= 1 domains; dims: 3 values per domain (each in [1, 65535], nz = 1
  * for D2Q9); beta: one value per domain in (0, 1).  opts as for elbm_create
- * (kernel is ignored).  Allocates both population buffers. */
+ * (kernel is ignored).  Allocates both population buffers.  A domain of more
+ * than 2^32 - 1 populations (Q nx ny nz) is ELBM_ERR_UNSUPPORTED: the batched
+ * kernels address each domain with 32-bit offsets (advance such a domain with
+ * elbm_create / elbm_step). */
 int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64_t *dims, const double *beta,
                       const elbm_opts *opts);
 void elbm_batch_destroy(elbm_batch_t *b);

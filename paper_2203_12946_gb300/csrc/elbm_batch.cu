@@ -14,6 +14,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <new>
@@ -50,6 +51,15 @@ struct elbm_batch {
     int num_sms = 0;
     int64_t steps = 0;
     std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs; // (n, starting buffer) -> graph
+    struct Persist {                                            // persistent launch plan per width
+        eelbm::PersistPlan plan;
+        int4 *segs = nullptr;
+        int *seg_off = nullptr;
+        unsigned *owners = nullptr;
+        unsigned *cnt = nullptr;
+    };
+    std::map<int, Persist> persist;
+    int *err_word = nullptr; // device: ELBM_ERR_TIMEOUT when a bounded device wait expired
     std::string err;
 };
 
@@ -187,6 +197,115 @@ void drop_graphs(elbm_batch_t *b)
     b->graphs.clear();
 }
 
+void drop_persist(elbm_batch_t *b)
+{
+    for (auto &kv : b->persist) {
+        cudaFree(kv.second.segs);
+        cudaFree(kv.second.seg_off);
+        cudaFree(kv.second.owners);
+        cudaFree(kv.second.cnt);
+    }
+    b->persist.clear();
+}
+
+// Static partition of the work items of width bx over every resident block
+// (blocks per SM from the occupancy calculator, times the SM count): block k
+// takes items [k I / G, (k + 1) I / G), cut into one segment per domain it touches.
+int build_persist(elbm_batch_t *b, int bx)
+{
+    if (b->persist.count(bx)) return ELBM_OK;
+    int st = build_items(b, bx);
+    if (st != ELBM_OK) return st;
+    const std::vector<int4> &it = b->items[bx];
+    const int64_t I = int64_t(it.size());
+    int per_sm = 0;
+    cudaError_t e = b->D == 2 ? eelbm::persist_blocks_per_sm_d2q9(b->opts.storage, bx, &per_sm)
+                              : eelbm::persist_blocks_per_sm_d3q27(b->opts.storage, bx, &per_sm);
+    if (e != cudaSuccess) return bcuda(b, e, "elbm_batch: occupancy of the persistent kernel");
+    if (per_sm < 1) return bfail(b, ELBM_ERR_UNSUPPORTED, "elbm_batch: persistent kernel cannot be resident");
+    const int G = int(std::min<int64_t>(int64_t(b->num_sms) * per_sm, I));
+    std::vector<int4> segs;
+    std::vector<int> seg_off(size_t(G) + 1, 0);
+    std::vector<unsigned> owners(b->doms.size(), 0u);
+    for (int k = 0; k < G; ++k) {
+        seg_off[k] = int(segs.size());
+        const int64_t w0 = int64_t(k) * I / G, w1 = int64_t(k + 1) * I / G;
+        for (int64_t w = w0; w < w1;) {
+            const int d = it[size_t(w)].x;
+            int64_t e1 = w;
+            while (e1 < w1 && it[size_t(e1)].x == d) ++e1;
+            segs.push_back(make_int4(d, int(w), int(e1), 0));
+            owners[size_t(d)] += 1u;
+            w = e1;
+        }
+    }
+    seg_off[G] = int(segs.size());
+    elbm_batch_t::Persist ps;
+    e = cudaMalloc(reinterpret_cast<void **>(&ps.segs), segs.size() * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&ps.seg_off), seg_off.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&ps.owners), owners.size() * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&ps.cnt), owners.size() * sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ps.segs, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ps.seg_off, seg_off.data(), seg_off.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ps.owners, owners.data(), owners.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(ps.segs);
+        cudaFree(ps.seg_off);
+        cudaFree(ps.owners);
+        cudaFree(ps.cnt);
+        return bcuda(b, e, "elbm_batch: persistent plan");
+    }
+    ps.plan.grid = G;
+    ps.plan.segs = ps.segs;
+    ps.plan.seg_off = ps.seg_off;
+    ps.plan.owners = ps.owners;
+    ps.plan.cnt = ps.cnt;
+    b->persist[bx] = ps;
+    return ELBM_OK;
+}
+
+// Steps per persistent launch: the per-domain counters reach steps x owners < 2^32.
+constexpr int kPersistChunk = 1 << 20;
+
+// Enqueues n steps as persistent launches (counters cleared before each).
+cudaError_t launch_persist(elbm_batch_t *b, int64_t n, int cur)
+{
+    const elbm_batch_t::Persist &ps = b->persist[b->bx];
+    const CollideParams p = params_of(b, 0.0); // beta comes from the domain table
+    cudaError_t e = cudaSuccess;
+    for (int64_t done = 0; done < n && e == cudaSuccess;) {
+        const int k = int(std::min<int64_t>(n - done, kPersistChunk));
+        e = cudaMemsetAsync(ps.cnt, 0, b->doms.size() * sizeof(unsigned), b->stream);
+        if (e == cudaSuccess)
+            e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], cur, k, b->d_doms,
+                                                            b->d_items[b->bx], ps.plan, b->bx, p, b->err_word,
+                                                            b->stream)
+                          : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], cur, k,
+                                                             b->d_doms, b->d_items[b->bx], ps.plan, b->bx, p,
+                                                             b->err_word, b->stream);
+        cur ^= k & 1;
+        done += k;
+    }
+    return e;
+}
+
+// Reads (and clears) the device error word after the stream has been synchronised.
+int check_flag(elbm_batch_t *b, const char *what)
+{
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, b->err_word, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, what);
+    if (flag != 0) {
+        cudaMemset(b->err_word, 0, sizeof(int));
+        return bfail(b, ELBM_ERR_TIMEOUT, "%s: a bounded device-side wait expired (the steps were not completed)",
+                     what);
+    }
+    return ELBM_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -223,6 +342,11 @@ int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64
         if (!(beta[d] > 0.0 && beta[d] < 1.0))
             return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_create: domain %d: beta = %g outside (0, 1)", d,
                          beta[d]);
+        if (uint64_t(Q) * uint64_t(dd[0] * dd[1] * dd[2]) > 0xffffffffull)
+            return bfail(nullptr, ELBM_ERR_UNSUPPORTED,
+                         "elbm_batch_create: domain %d: Q N = %lld populations exceed the 32-bit offsets of the "
+                         "batched kernels (at most 2^32 - 1)",
+                         d, (long long)(Q * dd[0] * dd[1] * dd[2]));
         BatchDomain &m = doms[d];
         m.nx = int(dd[0]);
         m.ny = int(dd[1]);
@@ -265,6 +389,8 @@ int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_doms, doms.data(), doms.size() * sizeof(BatchDomain), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->acc), sizeof(DiagAcc));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->err_word), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->err_word, 0, sizeof(int));
     if (e != cudaSuccess) {
         elbm_batch_destroy(b);
         return bcuda(nullptr, e, "elbm_batch_create: device allocation");
@@ -291,6 +417,8 @@ void elbm_batch_destroy(elbm_batch_t *b)
     cudaFree(b->d_doms);
     cudaFree(b->stage);
     cudaFree(b->acc);
+    cudaFree(b->err_word);
+    drop_persist(b);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -343,7 +471,8 @@ int elbm_batch_step(elbm_batch_t *b, int64_t n, int mode)
 {
     if (!b) return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_step: batch is NULL");
     if (n < 0) return bfail(b, ELBM_ERR_ARG, "elbm_batch_step: n = %lld < 0", (long long)n);
-    if (mode != ELBM_BATCH_GRAPH && mode != ELBM_BATCH_LAUNCHES && mode != ELBM_BATCH_PER_DOMAIN)
+    if (mode != ELBM_BATCH_GRAPH && mode != ELBM_BATCH_LAUNCHES && mode != ELBM_BATCH_PER_DOMAIN &&
+        mode != ELBM_BATCH_PERSISTENT)
         return bfail(b, ELBM_ERR_ARG, "elbm_batch_step: unknown mode %d", mode);
     if (n == 0) return ELBM_OK;
     DeviceGuard guard(b->opts.device);
@@ -374,8 +503,13 @@ int elbm_batch_step(elbm_batch_t *b, int64_t n, int mode)
         }
         return ELBM_OK;
     }
-    // ELBM_BATCH_GRAPH: the n launches captured once per (n, starting buffer, width)
-    const std::pair<int64_t, int> key(n, b->cur + 2 * b->bx);
+    if (mode == ELBM_BATCH_PERSISTENT) {
+        int st = build_persist(b, b->bx);
+        if (st != ELBM_OK) return st;
+    }
+    // ELBM_BATCH_GRAPH: the n launches captured once per (n, starting buffer, width);
+    // ELBM_BATCH_PERSISTENT: the persistent launch(es) of n steps, captured likewise
+    const std::pair<int64_t, int> key(n, b->cur + 2 * b->bx + (mode == ELBM_BATCH_PERSISTENT ? 4096 : 0));
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         cudaGraph_t graph = nullptr;
@@ -383,9 +517,13 @@ int elbm_batch_step(elbm_batch_t *b, int64_t n, int mode)
         if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_step: cudaStreamBeginCapture");
         int c = b->cur;
         cudaError_t le = cudaSuccess;
-        for (int64_t k = 0; k < n && le == cudaSuccess; ++k) {
-            le = launch_batch(b, b->pop[c], b->pop[c ^ 1], b->bx);
-            c ^= 1;
+        if (mode == ELBM_BATCH_PERSISTENT) {
+            le = launch_persist(b, n, c);
+        } else {
+            for (int64_t k = 0; k < n && le == cudaSuccess; ++k) {
+                le = launch_batch(b, b->pop[c], b->pop[c ^ 1], b->bx);
+                c ^= 1;
+            }
         }
         e = cudaStreamEndCapture(b->stream, &graph);
         if (le != cudaSuccess) {
@@ -566,7 +704,7 @@ int elbm_batch_synchronize(elbm_batch_t *b)
     DeviceGuard guard(b->opts.device);
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_synchronize");
-    return ELBM_OK;
+    return check_flag(b, "elbm_batch_synchronize");
 }
 
 int elbm_batch_info(const elbm_batch_t *b, int *ndomains, int64_t *nodes, int *block_width)

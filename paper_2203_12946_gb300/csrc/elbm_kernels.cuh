@@ -527,6 +527,95 @@ __global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restr
 }
 
 // --------------------------------------------------------------------------
+// Persistent ensemble: one cooperative launch advances every domain by nsteps.
+// Block b owns a fixed run of work items (plan.segs, balanced on the host) and
+// steps it nsteps times.  Domains are independent, so a block waits only for the
+// other owners of the same domain: before step t on domain d, until cnt[d] has
+// counted t steps of each of its owners (release: stores, barrier, fence, atomic
+// add; acquire: bounded spin, fence, barrier).  Populations are read with plain
+// coherent loads, not through the read-only path, since the buffers change during
+// the launch; offsets inside a domain are 32-bit (Q N < 2^32 per domain, checked
+// when the batch is created).  Every wait is bounded (kWaitLimitNs of
+// %globaltimer, also abandoned once another block has flagged an error): on
+// expiry the block records ELBM_ERR_TIMEOUT in *err and returns.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ bool wait_count(const unsigned *cnt, unsigned target, const int *err)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+        if (v >= target) return true;
+        if (*(volatile const int *)err != 0 || global_ns() - t0 > kWaitLimitNs) return false;
+        __nanosleep(64);
+    }
+}
+
+template <class ST, int BX>
+__global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typename ST::S *pop1, int cur,
+                                                    int nsteps, const BatchDomain *__restrict__ doms,
+                                                    const int4 *__restrict__ items, PersistPlan plan,
+                                                    CollideParams p, int *err)
+{
+    using T = typename ST::T;
+    using S = typename ST::S;
+    __shared__ int s_ok;
+    const T rho0 = rho0_of<T>(p);
+    const int s0 = plan.seg_off[blockIdx.x], s1 = plan.seg_off[blockIdx.x + 1];
+    for (int t = 0; t < nsteps; ++t) {
+        const bool odd = ((cur + t) & 1) != 0;
+        const S *fin = odd ? pop1 : pop0;
+        S *fout = odd ? pop0 : pop1;
+        for (int sg = s0; sg < s1; ++sg) {
+            const int4 seg = plan.segs[sg];
+            if (t > 0) {
+                if (threadIdx.x == 0) {
+                    s_ok = wait_count(plan.cnt + seg.x, unsigned(t) * plan.owners[seg.x], err);
+                    if (!s_ok) atomicExch(err, ELBM_ERR_TIMEOUT);
+                    __threadfence();
+                }
+                __syncthreads();
+                if (!s_ok) return;
+            }
+            const BatchDomain dm = doms[seg.x];
+            p.beta = dm.beta;
+            p.beta_f = dm.beta_f;
+            const uint32_t nx = uint32_t(dm.nx), ny = uint32_t(dm.ny), nz = uint32_t(dm.nz), N = uint32_t(dm.N);
+            const S *in = fin + dm.off;
+            S *out = fout + dm.off;
+            for (int w = seg.y; w < seg.z; ++w) {
+                const int4 it = __ldg(items + w);
+                const uint32_t x = uint32_t(it.w) + threadIdx.x;
+                if (x >= nx) continue;
+                const uint32_t y = uint32_t(it.y), z = uint32_t(it.z);
+                const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+                const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+                const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+                T f[Q], xd[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+                    const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+                    const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+                    const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+                    f[i] = ST::load(in[uint32_t(i) * N + (sz * ny + sy) * nx + sx], T(weight(D, i)), rho0);
+                }
+                int br;
+                collide<D, T, true>(f, xd, p, &br);
+                const uint32_t n = (z * ny + y) * nx + x;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) out[uint32_t(i) * N + n] = ST::store(f[i], T(weight(D, i)), rho0);
+            }
+            __syncthreads(); // every store of this segment issued
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(plan.cnt + seg.x, 1u);
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // Adjoint of one step (f^{t+1} = collide(stream(f^t))): given gnext = dL/df^{t+1},
 // write gout = dL/df^t.  Per node x: the pre-collision populations F(x) are
 // pulled from f^t as in the step, h = J^T gnext(x) is the collision's VJP, and
@@ -832,6 +921,55 @@ cudaError_t ELBM_CAT(launch_step_batch, ELBM_SUFFIX)(int storage, const void *fi
     }
 #undef ELBM_BATCH_BX
     return cudaGetLastError();
+}
+
+cudaError_t ELBM_CAT(persist_blocks_per_sm, ELBM_SUFFIX)(int storage, int bx, int *blocks)
+{
+    using namespace ELBM_SUFFIX;
+    *blocks = 0;
+#define ELBM_PERSIST_OCC(BXV)                                                                          \
+    ELBM_STORAGE_SWITCH(storage, return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks,           \
+                                                                             k_step_persist<ST, BXV>, BXV, 0))
+    switch (bx) {
+    case 64: ELBM_PERSIST_OCC(64); break;
+    case 128: ELBM_PERSIST_OCC(128); break;
+    case 256: ELBM_PERSIST_OCC(256); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef ELBM_PERSIST_OCC
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ELBM_CAT(launch_step_persist, ELBM_SUFFIX)(int storage, void *pop0, void *pop1, int cur, int nsteps,
+                                                       const BatchDomain *doms, const int4 *items,
+                                                       const PersistPlan &plan, int bx, const CollideParams &p,
+                                                       int *err, cudaStream_t s)
+{
+    using namespace ELBM_SUFFIX;
+    if (nsteps <= 0 || plan.grid <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative; // all blocks resident: they wait on one another
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(unsigned(plan.grid));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define ELBM_PERSIST_BX(BXV)                                                                           \
+    cfg.blockDim = dim3(BXV);                                                                          \
+    ELBM_STORAGE_SWITCH(storage, return cudaLaunchKernelEx(&cfg, k_step_persist<ST, BXV>,               \
+                                                           static_cast<typename ST::S *>(pop0),        \
+                                                           static_cast<typename ST::S *>(pop1), cur,   \
+                                                           nsteps, doms, items, plan, p, err))
+    switch (bx) {
+    case 64: ELBM_PERSIST_BX(64); break;
+    case 128: ELBM_PERSIST_BX(128); break;
+    case 256: ELBM_PERSIST_BX(256); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef ELBM_PERSIST_BX
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t ELBM_CAT(launch_step_adjoint, ELBM_SUFFIX)(int storage, const void *fin, const void *gnext,

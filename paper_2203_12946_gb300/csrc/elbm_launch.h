@@ -23,6 +23,18 @@ struct BatchDomain {
     double beta;
 };
 
+// Static partition of one persistent ensemble launch (device arrays): block b
+// steps the work items of segments seg_off[b] .. seg_off[b+1]-1, each segment
+// {domain, first item, end item, 0} inside one domain; owners[d] blocks hold a
+// segment of domain d, and cnt[d] counts their finished (block, step) pairs.
+struct PersistPlan {
+    int grid = 0;
+    const int4 *segs = nullptr;
+    const int *seg_off = nullptr;
+    const unsigned *owners = nullptr;
+    unsigned *cnt = nullptr;
+};
+
 // Device-side accumulator of the diagnostics reduction (library scratch).
 struct DiagAcc {
     double sum[6];                 // mass, momentum x/y/z, H, sum of alpha
@@ -71,6 +83,11 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
     cudaError_t launch_step_batch_##SUFFIX(int storage, const void *fin, void *fout,                \
                                            const BatchDomain *doms, const int4 *items, int nitems,   \
                                            int bx, const CollideParams &p, cudaStream_t s);          \
+    cudaError_t launch_step_persist_##SUFFIX(int storage, void *pop0, void *pop1, int cur, int nsteps,  \
+                                             const BatchDomain *doms, const int4 *items,             \
+                                             const PersistPlan &plan, int bx, const CollideParams &p, \
+                                             int *err, cudaStream_t s);                              \
+    cudaError_t persist_blocks_per_sm_##SUFFIX(int storage, int bx, int *blocks);                   \
     cudaError_t launch_step_adjoint_##SUFFIX(int storage, const void *fin, const void *gnext,       \
                                              void *gout, const Geometry &g, const CollideParams &p,  \
                                              double *dforce, cudaStream_t s);                        \

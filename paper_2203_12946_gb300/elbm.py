@@ -34,7 +34,7 @@ ELBM_ALPHA_HIGHER, ELBM_ALPHA_LOWER, ELBM_ALPHA_LBGK, ELBM_ALPHA_ITERATE1 = 0, 1
 ELBM_B_DERIVED, ELBM_B_PRINTED = 0, 1
 ELBM_MEM_DEVICE, ELBM_MEM_HOST = 0, 1
 ELBM_KERNEL_AUTO, ELBM_KERNEL_DIRECT, ELBM_KERNEL_ROWS = 0, 1, 2
-ELBM_BATCH_GRAPH, ELBM_BATCH_LAUNCHES, ELBM_BATCH_PER_DOMAIN = 0, 1, 2
+ELBM_BATCH_GRAPH, ELBM_BATCH_LAUNCHES, ELBM_BATCH_PER_DOMAIN, ELBM_BATCH_PERSISTENT = 0, 1, 2, 3
 ELBM_BRANCH_CUTOFF, ELBM_BRANCH_SOLVED, ELBM_BRANCH_CLAMPED = 0, 1, 2
 ELBM_HIST_BINS = 256
 

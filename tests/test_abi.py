@@ -138,6 +138,7 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     (E.ELBM_D2Q9, [(8, 8, 1), (0, 8, 1)], [0.9, 0.9], E.ELBM_ERR_ARG),
     (E.ELBM_D3Q27, [(8, 8, 8), (70000, 2, 2)], [0.9, 0.9], E.ELBM_ERR_ARG),
     (E.ELBM_D3Q27, [(8, 8, 8), (4, 4, 4)], [0.9, 1.0], E.ELBM_ERR_ARG),
+    (E.ELBM_D3Q27, [(8, 8, 8), (2048, 2048, 64)], [0.9, 0.9], E.ELBM_ERR_UNSUPPORTED),
 ])
 def test_batch_create_rejects_bad_arguments(lib, lattice, dims, betas, code):
     with pytest.raises(E.ElbmError) as ei:

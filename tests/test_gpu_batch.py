@@ -1,11 +1,11 @@
 """Batched ensembles (one launch advances many independent domains) against the
-oracle, and the three stepping modes against each other.
+oracle, and the four stepping modes against each other.
 
 Each domain of a batch is an independent periodic lattice with its own size and
 beta; the oracle advances each one separately.  GRAPH and LAUNCHES run the same
 kernel launches (one replayed from a CUDA graph), so they agree bit for bit;
-PER_DOMAIN runs the single-domain kernel, which the compiler may contract
-differently, so it agrees to FP32 rounding.
+PER_DOMAIN runs the single-domain kernel and PERSISTENT the persistent one,
+which the compiler may contract differently, so they agree to FP32 rounding.
 """
 import numpy as np
 import pytest
@@ -34,7 +34,8 @@ def domain_state(D, dims, eps, seed):
     return f * inputs.population_noise(3 ** D, X.size, eps, seed=seed)
 
 
-@pytest.mark.parametrize("mode", [E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_LAUNCHES, E.ELBM_BATCH_PER_DOMAIN])
+@pytest.mark.parametrize("mode", [E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_LAUNCHES, E.ELBM_BATCH_PER_DOMAIN,
+                                  E.ELBM_BATCH_PERSISTENT])
 def test_fp64_batch_matches_oracle_per_domain(mode):
     dims = [(20, 14, 1), (37, 23, 1), (64, 16, 1), (9, 9, 1), (130, 3, 1)]
     betas = [0.9, 0.99, 0.999, 0.95, 0.97]
@@ -50,14 +51,15 @@ def test_fp64_batch_matches_oracle_per_domain(mode):
         assert np.max(np.abs(got[k] - want) / want) < 1e-12, k
 
 
-def test_fp64_d3q27_batch_matches_oracle():
+@pytest.mark.parametrize("mode", [E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_PERSISTENT])
+def test_fp64_d3q27_batch_matches_oracle(mode):
     dims = [(12, 10, 8), (7, 9, 5), (16, 4, 4)]
     betas = [0.99, 0.9, 0.995]
     f0 = [domain_state(3, d, 3e-3, seed=10 + k) for k, d in enumerate(dims)]
     with E.Ensemble(E.ELBM_D3Q27, dims, betas, storage="f64") as ens:
         for k in range(len(dims)):
             ens.set_populations(k, f0[k])
-        ens.step(4)
+        ens.step(4, mode)
         got = [ens.get_populations(k) for k in range(len(dims))]
     for k, d in enumerate(dims):
         want, *_ = O.step(3, d, f0[k], betas[k], nsteps=4)
@@ -74,7 +76,7 @@ def test_modes_agree_and_tune_keeps_state():
         rho, u = inputs.random_vortex_2d(d[0], rms=0.03, seed=100 + k)
         states.append((rho, u))
     outs = {}
-    for mode in (E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_LAUNCHES, E.ELBM_BATCH_PER_DOMAIN):
+    for mode in (E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_LAUNCHES, E.ELBM_BATCH_PER_DOMAIN, E.ELBM_BATCH_PERSISTENT):
         with E.Ensemble(E.ELBM_D2Q9, dims, betas, storage="f32") as ens:
             for k, (rho, u) in enumerate(states):
                 ens.init_equilibrium(k, rho, u)
@@ -92,8 +94,10 @@ def test_modes_agree_and_tune_keeps_state():
         a = outs[E.ELBM_BATCH_GRAPH][k].astype(np.float64)
         b = outs[E.ELBM_BATCH_LAUNCHES][k].astype(np.float64)
         c = outs[E.ELBM_BATCH_PER_DOMAIN][k].astype(np.float64)
+        d = outs[E.ELBM_BATCH_PERSISTENT][k].astype(np.float64)
         assert np.max(np.abs(a - b) / b) < 7 * 1e-6  # tune may pick another width
         assert np.max(np.abs(a - c) / c) < 7 * 1e-6
+        assert np.max(np.abs(a - d) / d) < 7 * 1e-6
 
 
 def test_ensemble_conserves_per_domain():
@@ -115,6 +119,35 @@ def test_ensemble_conserves_per_domain():
         assert abs(b["mass"] - a["mass"]) < 50 * 1e-8 * a["mass"]
         assert np.max(np.abs(np.array(b["momentum"]) - np.array(a["momentum"]))) < 50 * 1e-8 * a["mass"]
         assert b["n_nonpositive"] == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16dev"])
+def test_persistent_matches_graph_on_the_ensemble_workload(storage):
+    """The 16-domain random ensemble (sides 64..512, so large domains are shared by many
+    blocks of the persistent launch and some blocks span several small domains): 101
+    persistent steps, issued as 1 + 100 (both buffer parities), agree with the
+    graph-replayed launches to FP32 rounding, and synchronising reports no expired wait."""
+    rng = np.random.default_rng(20221203)
+    sides = rng.choice([64, 96, 128, 192, 256, 384, 512], size=16)
+    dims = [(int(s), int(s), 1) for s in sides]
+    betas = list(rng.uniform(0.9, 0.999, size=len(dims)))
+    outs = {}
+    for mode in (E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_PERSISTENT):
+        with E.Ensemble(E.ELBM_D2Q9, dims, betas, storage=storage) as ens:
+            for k, d in enumerate(dims):
+                rho, u = inputs.random_vortex_2d(d[0], rms=0.03, seed=k)
+                ens.init_equilibrium(k, rho, u)
+            ens.step(1, mode)
+            ens.step(100, mode)
+            ens.synchronize()
+            outs[mode] = [ens.get_populations(k) for k in range(len(dims))]
+    for k in range(len(dims)):
+        a, b = (outs[m][k] for m in (E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_PERSISTENT))
+        if storage == "f32":
+            assert np.max(np.abs(a.astype(np.float64) - b) / np.abs(b)) < 101 * 2e-7, k
+        else:  # deviations in FP16: equal or one rounding step apart
+            da, db = a.astype(np.float64), b.astype(np.float64)
+            assert np.max(np.abs(da - db)) <= 4 * 2.0 ** -11 * np.max(np.abs(db)) + 1e-6, k
 
 
 def test_batch_domain_errors():
