@@ -355,6 +355,15 @@ int elbm_batch_diagnostics(elbm_batch_t *b, int domain, elbm_diag *out, int64_t 
 int elbm_batch_get_populations(elbm_batch_t *b, int domain, void *dst, int where);
 int elbm_batch_set_populations(elbm_batch_t *b, int domain, const void *src, int where);
 int elbm_batch_synchronize(elbm_batch_t *b);
+/* Self-test of the PERSISTENT mode's failure detection (no counterpart in the
+ * paper).  Runs one two-step persistent launch in which every domain counts one
+ * owner more than hold a part of it, so that every wait before the second step
+ * expires after the bounded limit (1 s) -- no fault, no hang -- and checks that
+ * the launch ended and reported ELBM_ERR_TIMEOUT.  Returns ELBM_OK when it did
+ * (the error flag is cleared again); ELBM_ERR_CUDA if the expiry went unreported.
+ * The state is unchanged: the first step writes the spare buffer only.
+ * Synchronises; takes about a second. */
+int elbm_batch_check_wait_timeout(elbm_batch_t *b);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free diagnostics.  The paper has no counterpart: this is a

@@ -57,6 +57,7 @@ struct elbm_batch {
         int *seg_off = nullptr;
         unsigned *owners = nullptr;
         unsigned *cnt = nullptr;
+        std::vector<unsigned> h_owners; // host copy
     };
     std::map<int, Persist> persist;
     int *err_word = nullptr; // device: ELBM_ERR_TIMEOUT when a bounded device wait expired
@@ -263,6 +264,7 @@ int build_persist(elbm_batch_t *b, int bx)
     ps.plan.seg_off = ps.seg_off;
     ps.plan.owners = ps.owners;
     ps.plan.cnt = ps.cnt;
+    ps.h_owners = owners;
     b->persist[bx] = ps;
     return ELBM_OK;
 }
@@ -705,6 +707,45 @@ int elbm_batch_synchronize(elbm_batch_t *b)
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_synchronize");
     return check_flag(b, "elbm_batch_synchronize");
+}
+
+int elbm_batch_check_wait_timeout(elbm_batch_t *b)
+{
+    if (!b) return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_check_wait_timeout: batch is NULL");
+    DeviceGuard guard(b->opts.device);
+    int st = build_persist(b, b->bx);
+    if (st != ELBM_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_check_wait_timeout: synchronize");
+    if ((st = check_flag(b, "elbm_batch_check_wait_timeout")) != ELBM_OK) return st;
+    // every domain gets one owner more than hold a segment: that owner never arrives
+    const elbm_batch_t::Persist &ps = b->persist[b->bx];
+    std::vector<unsigned> ghost(ps.h_owners);
+    for (unsigned &o : ghost) o += 1u;
+    unsigned *d_ghost = nullptr;
+    e = cudaMalloc(reinterpret_cast<void **>(&d_ghost), ghost.size() * sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_ghost, ghost.data(), ghost.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ps.cnt, 0, ghost.size() * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) {
+        eelbm::PersistPlan plan = ps.plan;
+        plan.owners = d_ghost;
+        const CollideParams p = params_of(b, 0.0);
+        // two steps: step 0 writes the spare buffer, every wait before step 1 expires,
+        // so the current buffer (the state) is never written
+        e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2, b->d_doms,
+                                                        b->d_items[b->bx], plan, b->bx, p, b->err_word, b->stream)
+                      : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2,
+                                                         b->d_doms, b->d_items[b->bx], plan, b->bx, p, b->err_word,
+                                                         b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d_ghost);
+    if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_check_wait_timeout: launch");
+    st = check_flag(b, "elbm_batch_check_wait_timeout");
+    if (st == ELBM_ERR_TIMEOUT) return ELBM_OK; // detected, flag cleared
+    if (st != ELBM_OK) return st;
+    return bfail(b, ELBM_ERR_CUDA, "elbm_batch_check_wait_timeout: the expired wait was not reported");
 }
 
 int elbm_batch_info(const elbm_batch_t *b, int *ndomains, int64_t *nodes, int *block_width)

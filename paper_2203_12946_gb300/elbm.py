@@ -51,7 +51,8 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
             "elbm_batch_init_equilibrium", "elbm_batch_step", "elbm_batch_tune", "elbm_batch_moments",
             "elbm_batch_diagnostics", "elbm_batch_get_populations", "elbm_batch_set_populations",
             "elbm_batch_synchronize", "elbm_adjoint_step", "elbm_kinetic_energy", "elbm_equilibrium_vjp",
-            "elbm_subgrid_viscosity", "elbm_adjoint_step_force", "elbm_set_force", "elbm_step_diag"]
+            "elbm_subgrid_viscosity", "elbm_adjoint_step_force", "elbm_set_force", "elbm_step_diag",
+            "elbm_batch_check_wait_timeout"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -138,6 +139,7 @@ def load(build_if_missing: bool = True):
             "elbm_batch_get_populations": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
             "elbm_batch_set_populations": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
             "elbm_batch_synchronize": (ctypes.c_int, [P]),
+            "elbm_batch_check_wait_timeout": (ctypes.c_int, [P]),
             "elbm_adjoint_step": (ctypes.c_int, [P, P, P, P]),
             "elbm_kinetic_energy": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_double), P]),
             "elbm_equilibrium_vjp": (ctypes.c_int, [P, P, P, P, P, P]),
@@ -577,6 +579,10 @@ def elbm_batch_set_populations(b, domain, src, where=ELBM_MEM_HOST) -> None:
 
 def elbm_batch_synchronize(b) -> None:
     _bcheck(b, load().elbm_batch_synchronize(b), "elbm_batch_synchronize")
+
+
+def elbm_batch_check_wait_timeout(b) -> None:
+    _bcheck(b, load().elbm_batch_check_wait_timeout(b), "elbm_batch_check_wait_timeout")
 
 
 class Ensemble:

@@ -150,6 +150,28 @@ def test_persistent_matches_graph_on_the_ensemble_workload(storage):
             assert np.max(np.abs(da - db)) <= 4 * 2.0 ** -11 * np.max(np.abs(db)) + 1e-6, k
 
 
+def test_persistent_wait_expiry_is_reported_and_the_context_survives():
+    """Failure detection of the persistent mode without a GPU fault: a launch whose waits
+    cannot be satisfied (one owner per domain that never arrives, injected on the host)
+    ends after the bounded wait and reports ELBM_ERR_TIMEOUT; the state is untouched and
+    the batch keeps stepping correctly afterwards."""
+    dims = [(64, 48, 1), (96, 96, 1), (33, 20, 1)]
+    betas = [0.95, 0.99, 0.9]
+    f0 = [domain_state(2, d, 3e-3, seed=30 + k).astype(np.float32) for k, d in enumerate(dims)]
+    with E.Ensemble(E.ELBM_D2Q9, dims, betas, storage="f32") as ens:
+        for k in range(len(dims)):
+            ens.set_populations(k, f0[k])
+        E.elbm_batch_check_wait_timeout(ens.b)
+        for k in range(len(dims)):
+            assert np.array_equal(ens.get_populations(k), f0[k])
+        ens.step(3, E.ELBM_BATCH_PERSISTENT)
+        ens.synchronize()
+        got = [ens.get_populations(k) for k in range(len(dims))]
+    for k, d in enumerate(dims):
+        want, *_ = O.step(2, d, f0[k].astype(np.float64), betas[k], nsteps=3)
+        assert np.max(np.abs(got[k] - want) / want) < 3 * 2e-6, k
+
+
 def test_batch_domain_errors():
     with E.Ensemble(E.ELBM_D2Q9, [(16, 16, 1)], [0.9], storage="f32") as ens:
         with pytest.raises(E.ElbmError) as ei:
