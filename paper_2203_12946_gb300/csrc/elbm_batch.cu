@@ -58,6 +58,7 @@ struct elbm_batch {
         unsigned *owners = nullptr;
         unsigned *cnt = nullptr;
         std::vector<unsigned> h_owners; // host copy
+        int max_steps = 1;              // steps per launch that keep steps x owners below 2^32
     };
     std::map<int, Persist> persist;
     int *err_word = nullptr; // device: ELBM_ERR_TIMEOUT when a bounded device wait expired
@@ -265,12 +266,11 @@ int build_persist(elbm_batch_t *b, int bx)
     ps.plan.owners = ps.owners;
     ps.plan.cnt = ps.cnt;
     ps.h_owners = owners;
+    const unsigned max_owner = *std::max_element(owners.begin(), owners.end());
+    ps.max_steps = int(std::min<uint64_t>(uint64_t(1) << 20, 0xffffffffull / (uint64_t(max_owner) + 1u)));
     b->persist[bx] = ps;
     return ELBM_OK;
 }
-
-// Steps per persistent launch: the per-domain counters reach steps x owners < 2^32.
-constexpr int kPersistChunk = 1 << 20;
 
 // Enqueues n steps as persistent launches (counters cleared before each).
 cudaError_t launch_persist(elbm_batch_t *b, int64_t n, int cur)
@@ -279,7 +279,7 @@ cudaError_t launch_persist(elbm_batch_t *b, int64_t n, int cur)
     const CollideParams p = params_of(b, 0.0); // beta comes from the domain table
     cudaError_t e = cudaSuccess;
     for (int64_t done = 0; done < n && e == cudaSuccess;) {
-        const int k = int(std::min<int64_t>(n - done, kPersistChunk));
+        const int k = int(std::min<int64_t>(n - done, ps.max_steps)); // counters stay below 2^32
         e = cudaMemsetAsync(ps.cnt, 0, b->doms.size() * sizeof(unsigned), b->stream);
         if (e == cudaSuccess)
             e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], cur, k, b->d_doms,
