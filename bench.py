@@ -386,8 +386,11 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, dt, desc = oracle_time(*oracle_prepare(args.cpu_slab), args.cpu_steps)
+        # and on one core: 2 steps of a 256 x 256 x 8 slab (~1M node updates)
+        rate1, _, dt1, desc1 = oracle_time(*oracle_prepare(8), 2, nthreads=1)
         line["cpu_baseline"] = {"value": rate, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-                                "sample": desc, "seconds": dt}
+                                "sample": desc, "seconds": dt,
+                                "single_core": {"value": rate1, "sample": desc1, "seconds": dt1}}
     sim.close()
     rep.close()
     if rank == 0:
