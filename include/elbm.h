@@ -323,11 +323,13 @@ typedef struct elbm_batch elbm_batch_t;
  * slot, own fixed runs of work items and wait only for the other owners of the
  * same domain between steps; those waits are bounded (1 s), and one that
  * expires leaves the steps incomplete and makes the next elbm_batch_synchronize
- * return ELBM_ERR_TIMEOUT. */
+ * return ELBM_ERR_TIMEOUT.  AUTO: whichever of GRAPH and PERSISTENT
+ * elbm_batch_tune_persistent found faster (GRAPH until it has run). */
 #define ELBM_BATCH_GRAPH 0
 #define ELBM_BATCH_LAUNCHES 1
 #define ELBM_BATCH_PER_DOMAIN 2
 #define ELBM_BATCH_PERSISTENT 3
+#define ELBM_BATCH_AUTO 4
 
 /* ndomains >= 1 domains; dims: 3 values per domain (each in [1, 65535], nz = 1
  * for D2Q9); beta: one value per domain in (0, 1).  opts as for elbm_create
@@ -350,6 +352,15 @@ int elbm_batch_step(elbm_batch_t *b, int64_t n, int mode);
  * state is unchanged -- and keeps the fastest.  chosen (may be NULL) receives
  * it; ms_per_step (may be NULL) three timings in that order.  Synchronises. */
 int elbm_batch_tune(elbm_batch_t *b, int *chosen, double *ms_per_step);
+/* Times the PERSISTENT mode at the work-item widths 64, 128 and 256 and the
+ * batched launches at the width elbm_batch_tune chose (run first if it has not
+ * been), 2 untimed and 50 timed steps each, advancing a copy of the state (the
+ * state is restored afterwards); keeps the fastest width for PERSISTENT and sets
+ * what ELBM_BATCH_AUTO issues: PERSISTENT if its steps were faster, else GRAPH.  chosen_mode
+ * (may be NULL) receives that mode; ms_per_step (may be NULL) the three
+ * persistent timings.  Allocates one temporary copy of a population buffer;
+ * synchronises. */
+int elbm_batch_tune_persistent(elbm_batch_t *b, int *chosen_mode, double *ms_per_step);
 int elbm_batch_moments(elbm_batch_t *b, int domain, double *rho_out, double *u_out, int where);
 int elbm_batch_diagnostics(elbm_batch_t *b, int domain, elbm_diag *out, int64_t *alpha_hist);
 int elbm_batch_get_populations(elbm_batch_t *b, int domain, void *dst, int where);

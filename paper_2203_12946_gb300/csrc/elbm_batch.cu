@@ -62,6 +62,9 @@ struct elbm_batch {
     };
     std::map<int, Persist> persist;
     int *err_word = nullptr; // device: ELBM_ERR_TIMEOUT when a bounded device wait expired
+    int pbx = 64;                             // work-item width of the persistent mode (tuned)
+    int auto_mode = ELBM_BATCH_GRAPH;         // what ELBM_BATCH_AUTO issues (tuned)
+    double graph_ms = 0.0;                    // per-step time of the width trials (0: not run)
     std::string err;
 };
 
@@ -275,7 +278,7 @@ int build_persist(elbm_batch_t *b, int bx)
 // Enqueues n steps as persistent launches (counters cleared before each).
 cudaError_t launch_persist(elbm_batch_t *b, int64_t n, int cur)
 {
-    const elbm_batch_t::Persist &ps = b->persist[b->bx];
+    const elbm_batch_t::Persist &ps = b->persist[b->pbx];
     const CollideParams p = params_of(b, 0.0); // beta comes from the domain table
     cudaError_t e = cudaSuccess;
     for (int64_t done = 0; done < n && e == cudaSuccess;) {
@@ -283,10 +286,10 @@ cudaError_t launch_persist(elbm_batch_t *b, int64_t n, int cur)
         e = cudaMemsetAsync(ps.cnt, 0, b->doms.size() * sizeof(unsigned), b->stream);
         if (e == cudaSuccess)
             e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], cur, k, b->d_doms,
-                                                            b->d_items[b->bx], ps.plan, b->bx, p, b->err_word,
+                                                            b->d_items[b->pbx], ps.plan, b->pbx, p, b->err_word,
                                                             b->stream)
                           : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], cur, k,
-                                                             b->d_doms, b->d_items[b->bx], ps.plan, b->bx, p,
+                                                             b->d_doms, b->d_items[b->pbx], ps.plan, b->pbx, p,
                                                              b->err_word, b->stream);
         cur ^= k & 1;
         done += k;
@@ -474,8 +477,9 @@ int elbm_batch_step(elbm_batch_t *b, int64_t n, int mode)
     if (!b) return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_step: batch is NULL");
     if (n < 0) return bfail(b, ELBM_ERR_ARG, "elbm_batch_step: n = %lld < 0", (long long)n);
     if (mode != ELBM_BATCH_GRAPH && mode != ELBM_BATCH_LAUNCHES && mode != ELBM_BATCH_PER_DOMAIN &&
-        mode != ELBM_BATCH_PERSISTENT)
+        mode != ELBM_BATCH_PERSISTENT && mode != ELBM_BATCH_AUTO)
         return bfail(b, ELBM_ERR_ARG, "elbm_batch_step: unknown mode %d", mode);
+    if (mode == ELBM_BATCH_AUTO) mode = b->auto_mode;
     if (n == 0) return ELBM_OK;
     DeviceGuard guard(b->opts.device);
     cudaError_t e;
@@ -506,12 +510,13 @@ int elbm_batch_step(elbm_batch_t *b, int64_t n, int mode)
         return ELBM_OK;
     }
     if (mode == ELBM_BATCH_PERSISTENT) {
-        int st = build_persist(b, b->bx);
+        int st = build_persist(b, b->pbx);
         if (st != ELBM_OK) return st;
     }
     // ELBM_BATCH_GRAPH: the n launches captured once per (n, starting buffer, width);
     // ELBM_BATCH_PERSISTENT: the persistent launch(es) of n steps, captured likewise
-    const std::pair<int64_t, int> key(n, b->cur + 2 * b->bx + (mode == ELBM_BATCH_PERSISTENT ? 4096 : 0));
+    const std::pair<int64_t, int> key(n, mode == ELBM_BATCH_PERSISTENT ? 4096 + b->cur + 2 * b->pbx
+                                                                      : b->cur + 2 * b->bx);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         cudaGraph_t graph = nullptr;
@@ -586,7 +591,86 @@ int elbm_batch_tune(elbm_batch_t *b, int *chosen, double *ms_per_step)
     cudaEventDestroy(e1);
     if (best_bx != b->bx) drop_graphs(b);
     b->bx = best_bx;
+    b->graph_ms = best / 5.0; // marks the width trials as done
     if (chosen) *chosen = best_bx;
+    return ELBM_OK;
+}
+
+int elbm_batch_tune_persistent(elbm_batch_t *b, int *chosen_mode, double *ms_per_step)
+{
+    if (!b) return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_tune_persistent: batch is NULL");
+    DeviceGuard guard(b->opts.device);
+    static const int cands[3] = {64, 128, 256};
+    constexpr int kTrial = 50; // timed steps per trial, after 2 untimed ones
+    if (b->graph_ms <= 0.0) {  // the graph's width, from its own trials
+        int st = elbm_batch_tune(b, nullptr, nullptr);
+        if (st != ELBM_OK) return st;
+    }
+    // the trials advance a copy of the state: save the current buffer, restore it after
+    const size_t bytes = b->total_elems * b->elem;
+    void *save = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&save, bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save, b->pop[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // every trial starts from the saved state (steps near equilibrium are cheaper)
+    auto restore = [&]() {
+        return cudaMemcpyAsync(b->pop[b->cur], save, bytes, cudaMemcpyDeviceToDevice, b->stream);
+    };
+    // the batched launches at the graph's width, kTrial steps issued back to back
+    float graph_ms = 0.0f;
+    if (e == cudaSuccess) {
+        int c = b->cur;
+        for (int k = 0; k < 2 + kTrial && e == cudaSuccess; ++k) {
+            if (k == 2) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = launch_batch(b, b->pop[c], b->pop[c ^ 1], b->bx);
+            c ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&graph_ms, e0, e1);
+    }
+    double best = 1e300;
+    int best_bx = b->pbx, st = ELBM_OK;
+    for (int c = 0; c < 3 && e == cudaSuccess && st == ELBM_OK; ++c) {
+        const int keep = b->pbx;
+        b->pbx = cands[c];
+        st = build_persist(b, b->pbx);
+        if (st == ELBM_OK) {
+            e = restore();
+            if (e == cudaSuccess) e = launch_persist(b, 2, b->cur);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = launch_persist(b, kTrial, b->cur);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess) {
+                if (ms_per_step) ms_per_step[c] = ms / kTrial;
+                if (ms < best) {
+                    best = ms;
+                    best_bx = cands[c];
+                }
+            }
+        }
+        b->pbx = keep;
+    }
+    cudaError_t er = cudaSuccess;
+    if (save) {
+        er = restore();
+        if (er == cudaSuccess) er = cudaStreamSynchronize(b->stream);
+        cudaFree(save);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != ELBM_OK) return st;
+    if (e == cudaSuccess) e = er;
+    if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_tune_persistent");
+    if ((st = check_flag(b, "elbm_batch_tune_persistent")) != ELBM_OK) return st;
+    b->pbx = best_bx;
+    b->auto_mode = best < graph_ms ? ELBM_BATCH_PERSISTENT : ELBM_BATCH_GRAPH;
+    if (chosen_mode) *chosen_mode = b->auto_mode;
     return ELBM_OK;
 }
 
@@ -713,13 +797,13 @@ int elbm_batch_check_wait_timeout(elbm_batch_t *b)
 {
     if (!b) return bfail(nullptr, ELBM_ERR_ARG, "elbm_batch_check_wait_timeout: batch is NULL");
     DeviceGuard guard(b->opts.device);
-    int st = build_persist(b, b->bx);
+    int st = build_persist(b, b->pbx);
     if (st != ELBM_OK) return st;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_check_wait_timeout: synchronize");
     if ((st = check_flag(b, "elbm_batch_check_wait_timeout")) != ELBM_OK) return st;
     // every domain gets one owner more than hold a segment: that owner never arrives
-    const elbm_batch_t::Persist &ps = b->persist[b->bx];
+    const elbm_batch_t::Persist &ps = b->persist[b->pbx];
     std::vector<unsigned> ghost(ps.h_owners);
     for (unsigned &o : ghost) o += 1u;
     unsigned *d_ghost = nullptr;
@@ -734,10 +818,10 @@ int elbm_batch_check_wait_timeout(elbm_batch_t *b)
         // two steps: step 0 writes the spare buffer, every wait before step 1 expires,
         // so the current buffer (the state) is never written
         e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2, b->d_doms,
-                                                        b->d_items[b->bx], plan, b->bx, p, b->err_word, b->stream)
+                                                        b->d_items[b->pbx], plan, b->pbx, p, b->err_word, b->stream)
                       : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2,
-                                                         b->d_doms, b->d_items[b->bx], plan, b->bx, p, b->err_word,
-                                                         b->stream);
+                                                         b->d_doms, b->d_items[b->pbx], plan, b->pbx, p,
+                                                         b->err_word, b->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     cudaFree(d_ghost);

@@ -34,7 +34,7 @@ ELBM_ALPHA_HIGHER, ELBM_ALPHA_LOWER, ELBM_ALPHA_LBGK, ELBM_ALPHA_ITERATE1 = 0, 1
 ELBM_B_DERIVED, ELBM_B_PRINTED = 0, 1
 ELBM_MEM_DEVICE, ELBM_MEM_HOST = 0, 1
 ELBM_KERNEL_AUTO, ELBM_KERNEL_DIRECT, ELBM_KERNEL_ROWS = 0, 1, 2
-ELBM_BATCH_GRAPH, ELBM_BATCH_LAUNCHES, ELBM_BATCH_PER_DOMAIN, ELBM_BATCH_PERSISTENT = 0, 1, 2, 3
+ELBM_BATCH_GRAPH, ELBM_BATCH_LAUNCHES, ELBM_BATCH_PER_DOMAIN, ELBM_BATCH_PERSISTENT, ELBM_BATCH_AUTO = 0, 1, 2, 3, 4
 ELBM_BRANCH_CUTOFF, ELBM_BRANCH_SOLVED, ELBM_BRANCH_CLAMPED = 0, 1, 2
 ELBM_HIST_BINS = 256
 
@@ -52,7 +52,7 @@ EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_d
             "elbm_batch_diagnostics", "elbm_batch_get_populations", "elbm_batch_set_populations",
             "elbm_batch_synchronize", "elbm_adjoint_step", "elbm_kinetic_energy", "elbm_equilibrium_vjp",
             "elbm_subgrid_viscosity", "elbm_adjoint_step_force", "elbm_set_force", "elbm_step_diag",
-            "elbm_batch_check_wait_timeout"]
+            "elbm_batch_check_wait_timeout", "elbm_batch_tune_persistent"]
 
 
 class elbm_opts(ctypes.Structure):
@@ -140,6 +140,8 @@ def load(build_if_missing: bool = True):
             "elbm_batch_set_populations": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
             "elbm_batch_synchronize": (ctypes.c_int, [P]),
             "elbm_batch_check_wait_timeout": (ctypes.c_int, [P]),
+            "elbm_batch_tune_persistent": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int),
+                                                          ctypes.POINTER(ctypes.c_double)]),
             "elbm_adjoint_step": (ctypes.c_int, [P, P, P, P]),
             "elbm_kinetic_energy": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_double), P]),
             "elbm_equilibrium_vjp": (ctypes.c_int, [P, P, P, P, P, P]),
@@ -555,6 +557,13 @@ def elbm_batch_tune(b):
     return chosen.value, list(ms)
 
 
+def elbm_batch_tune_persistent(b):
+    mode = ctypes.c_int(0)
+    ms = (ctypes.c_double * 3)()
+    _bcheck(b, load().elbm_batch_tune_persistent(b, ctypes.byref(mode), ms), "elbm_batch_tune_persistent")
+    return mode.value, list(ms)
+
+
 def elbm_batch_moments(b, domain, rho_out, u_out, where=ELBM_MEM_HOST) -> None:
     _bcheck(b, load().elbm_batch_moments(b, int(domain), _ptr(rho_out), _ptr(u_out), int(where)),
             "elbm_batch_moments")
@@ -640,6 +649,10 @@ class Ensemble:
 
     def tune(self):
         return elbm_batch_tune(self.b)
+
+    def tune_persistent(self):
+        """(mode ELBM_BATCH_AUTO will issue, ms per step of the persistent mode per width)."""
+        return elbm_batch_tune_persistent(self.b)
 
     def moments(self, d):
         N = self.nodes(d)

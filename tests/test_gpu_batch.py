@@ -172,6 +172,27 @@ def test_persistent_wait_expiry_is_reported_and_the_context_survives():
         assert np.max(np.abs(got[k] - want) / want) < 3 * 2e-6, k
 
 
+def test_persistent_tuner_keeps_the_state_and_auto_follows_its_choice():
+    rng = np.random.default_rng(11)
+    sides = rng.choice([64, 96, 128], size=10)
+    dims = [(int(s), int(s), 1) for s in sides]
+    betas = list(rng.uniform(0.9, 0.999, size=len(dims)))
+    outs = {}
+    for run in ("auto", "explicit"):
+        with E.Ensemble(E.ELBM_D2Q9, dims, betas, storage="f32") as ens:
+            for k, d in enumerate(dims):
+                rho, u = inputs.random_vortex_2d(d[0], rms=0.03, seed=200 + k)
+                ens.init_equilibrium(k, rho, u)
+            before = [ens.get_populations(k).copy() for k in range(len(dims))]
+            mode, ms = ens.tune_persistent()
+            assert mode in (E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_PERSISTENT) and all(m > 0 for m in ms)
+            assert all(np.array_equal(a, ens.get_populations(k)) for k, a in enumerate(before))
+            ens.step(5, E.ELBM_BATCH_AUTO if run == "auto" else mode)
+            ens.synchronize()
+            outs[run] = [ens.get_populations(k) for k in range(len(dims))]
+    assert all(np.array_equal(a, b) for a, b in zip(outs["auto"], outs["explicit"]))
+
+
 def test_batch_domain_errors():
     with E.Ensemble(E.ELBM_D2Q9, [(16, 16, 1)], [0.9], storage="f32") as ens:
         with pytest.raises(E.ElbmError) as ei:
