@@ -691,7 +691,9 @@ def run_adjoint(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 5000 for the benchmark workload, the Taylor-Green "
+                         "configuration's length; 2000 for the others)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-slab", type=int, default=128,
@@ -716,6 +718,8 @@ def main():
     ap.add_argument("--L", type=int, default=L, help="domain side (profiling runs only; "
                     "the benchmark workload is 256)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5000 if args.workload == "tgv3d" else 2000
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.L != L:

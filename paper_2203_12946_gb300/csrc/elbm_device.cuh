@@ -607,10 +607,15 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         // |x|max^3 = 1.25e-7 of M2 times their coefficients (1/8 in c1, 1/4 in c), and
         // alpha moves by at most ~3e-8 relative, below FP32 rounding.  The series forms
         // need no reciprocal per population and no second pass for b.
+        // The form is chosen once per warp, from its largest |x|max among the lanes
+        // solving here: a warp whose lanes straddle a threshold runs the longer form
+        // on all of them instead of each form in turn (the forms agree below FP32
+        // rounding, so a lane's path length does not depend on which one it got).
         constexpr float kSeriesX = 0.02f, kShortX = 0.005f;
-        const bool series = xabs < kSeriesX;
+        const int form = __reduce_max_sync(__activemask(), xabs < kShortX ? 0 : (xabs < kSeriesX ? 1 : 2));
+        const bool series = form < 2;
         float sb1, sc1, sc, s3, s4, s5 = 0.0f, s6 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f, m6 = 0.0f;
-        if (xabs < kShortX) {
+        if (form == 0) {
             float2 M2 = f2(0.0f), M3 = f2(0.0f), M4 = f2(0.0f), S3 = f2(0.0f), S4 = f2(0.0f);
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
