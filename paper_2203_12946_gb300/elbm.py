@@ -546,7 +546,7 @@ def elbm_batch_init_equilibrium(b, domain, rho, u, where=ELBM_MEM_HOST) -> None:
             "elbm_batch_init_equilibrium")
 
 
-def elbm_batch_step(b, n=1, mode=ELBM_BATCH_GRAPH) -> None:
+def elbm_batch_step(b, n=1, mode=ELBM_BATCH_AUTO) -> None:
     _bcheck(b, load().elbm_batch_step(b, int(n), int(mode)), "elbm_batch_step")
 
 
@@ -644,7 +644,9 @@ class Ensemble:
         rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
         elbm_batch_init_equilibrium(self.b, d, rho, u, ELBM_MEM_HOST)
 
-    def step(self, n=1, mode=ELBM_BATCH_GRAPH):
+    def step(self, n=1, mode=ELBM_BATCH_AUTO):
+        """n steps of every domain; AUTO issues the form tune_persistent() found faster
+        (the graph of batched launches until it has run)."""
         elbm_batch_step(self.b, n, mode)
 
     def tune(self):
