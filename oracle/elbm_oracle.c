@@ -19,7 +19,7 @@
  * and the adjoint of the step (node Jacobians by central differences), both
  * used to check gradients.
  *
- * Readings where the paper is ambiguous (each also listed in the design doc):
+ * Readings where the paper is ambiguous:
  *  R1  the product-form equilibrium carries one factor Upsilon_a per axis
  *      (Sec. I, D2Q9/D3Q27 equilibrium), and with theta0 = 1/3 the exponent
  *      c_ia/sqrt(3 theta0) is c_ia in {-1, 0, 1};

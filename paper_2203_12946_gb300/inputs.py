@@ -6,7 +6,7 @@ coordinates) and plain random numbers.  Both the CUDA path and the CPU oracle
 turn these into populations with their own equilibrium code.
 
 Workloads (the paper measures on no public dataset; these stand in for its
-flows, see DESIGN.md):
+flows):
 
 * ``taylor_green_2d``  -- periodic 2D Taylor-Green vortex, k = 2 pi / L,
   u_x = u0 sin(kx) cos(ky), u_y = -u0 cos(kx) sin(ky),
