@@ -75,6 +75,11 @@ MUTANTS = {
                                  [A + "::test_force_term_moments"]),
     "force_sign": ("f[i] += feq1[i] - feq0[i];", "f[i] += feq0[i] - feq1[i];",
                    [A + "::test_uniform_flow_accelerates_linearly"]),
+    "entropy_drops_minus_one": ("H += f[i] * (log(f[i] / w[i]) - 1.0);", "H += f[i] * log(f[i] / w[i]);",
+                                [P + "::test_H_of_uniform_rest_states"]),
+    "iterate1_newton_sign": ("return alpha_lower - or_F(Q, f, x, alpha_lower) / or_dF(Q, f, x, alpha_lower);",
+                             "return alpha_lower + or_F(Q, f, x, alpha_lower) / or_dF(Q, f, x, alpha_lower);",
+                             [P + "::test_iterate1_and_table3_magnitudes"]),
     "adjoint_push_direction": ("g_t[(int64_t)i * N + (sz * ny + sy) * nx + sx] = h[i];",
                                "g_t[(int64_t)i * N + n] = h[i];",
                                [A + "::test_step_adjoint_transpose_identity"]),

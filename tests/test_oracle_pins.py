@@ -133,6 +133,21 @@ def test_equilibrium_minimises_H(D):
             assert O.H(feq + d, w) > H0
 
 
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_H_of_uniform_rest_states(D):
+    """Eq. hdef, H = <f, log(f/w) - 1>: a node at rest, f = rho w, has H = rho (log rho - 1)
+    (the mass and entropy-difference tests cannot see the -1 or a constant in the log: the
+    collision conserves <f,1>), and a field of N such nodes N times that."""
+    c, w = O.lattice(D)
+    for rho in (0.5, 1.0, 2.7):
+        assert abs(O.H(rho * w, w) - rho * (np.log(rho) - 1.0)) < 1e-14
+    if D > 1:
+        dims = (5, 4, 3) if D == 3 else (7, 3, 1)
+        N = int(np.prod(dims))
+        f = np.repeat((1.3 * w)[:, None], N, axis=1)
+        assert abs(O.H_total(D, f) - N * 1.3 * (np.log(1.3) - 1.0)) < 1e-12
+
+
 @pytest.mark.parametrize("D", [2, 3])
 def test_equilibrium_series_matches_to_third_order(D):
     """Sec. I: the entropic equilibrium agrees with the polynomial equilibrium (Eq. histeq)
