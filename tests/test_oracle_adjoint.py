@@ -72,6 +72,19 @@ def test_step_adjoint_transpose_identity(D, dims):
     assert abs(lhs - rhs) <= 1e-7 * np.linalg.norm(g) * np.linalg.norm(v)
 
 
+def test_kinetic_energy_of_uniform_flows():
+    """L = 1/2 sum_n rho_n |u_n|^2 (the rollout loss): N nodes of the equilibrium at rho, u
+    give N rho |u|^2 / 2; the loss is blind to a rest state's density."""
+    for D in (2, 3):
+        u = np.array([0.03, -0.02, 0.01])[:D]
+        N = 12
+        f = O.init_equilibrium(D, np.full(N, 1.2), np.repeat(u[:, None], N, axis=1))
+        L, _ = O.kinetic_energy(D, f, want_grad=False)
+        assert abs(L - N * 0.5 * 1.2 * float(u @ u)) < 1e-15 * N
+        L0, _ = O.kinetic_energy(D, O.init_equilibrium(D, np.full(N, 1.7), np.zeros((D, N))), want_grad=False)
+        assert abs(L0) < 1e-30
+
+
 def test_kinetic_energy_gradient():
     rng = np.random.default_rng(41)
     D, N = 2, 30

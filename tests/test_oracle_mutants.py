@@ -80,6 +80,8 @@ MUTANTS = {
     "iterate1_newton_sign": ("return alpha_lower - or_F(Q, f, x, alpha_lower) / or_dF(Q, f, x, alpha_lower);",
                              "return alpha_lower + or_F(Q, f, x, alpha_lower) / or_dF(Q, f, x, alpha_lower);",
                              [P + "::test_iterate1_and_table3_magnitudes"]),
+    "kinetic_energy_half": ("L += 0.5 * rho * uu;", "L += rho * uu;",
+                            [A + "::test_kinetic_energy_of_uniform_flows"]),
     "adjoint_push_direction": ("g_t[(int64_t)i * N + (sz * ny + sy) * nx + sx] = h[i];",
                                "g_t[(int64_t)i * N + n] = h[i];",
                                [A + "::test_step_adjoint_transpose_identity"]),
