@@ -7,9 +7,14 @@
 // single-domain kernels (init, moments, diagnostics) run on a domain's block
 // unchanged.  A step is one launch of k_step_batch over a host-built table of
 // work items (domain, y, z, x0); elbm_batch_step can also replay the n launches
-// as one CUDA graph, or launch the single-domain kernel once per domain (the
-// comparison the batched form is measured against).  elbm_batch_tune times the
-// candidate block widths on the current state without changing it.
+// as one CUDA graph, advance all n steps in one cooperative launch of
+// k_step_persist (blocks own fixed runs of work items and wait, with bounded
+// spins, only for the other owners of their domains), or launch the
+// single-domain kernel once per domain (the comparison the batched forms are
+// measured against).  elbm_batch_tune times the candidate block widths on the
+// current state without changing it; elbm_batch_tune_persistent times the
+// persistent launch against the batched launches on a copy of the state and
+// sets which one ELBM_BATCH_AUTO issues.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
