@@ -610,7 +610,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         // The form is chosen once per warp, from its largest |x|max among the lanes
         // solving here: a warp whose lanes straddle a threshold runs the longer form
         // on all of them instead of each form in turn (the forms agree below FP32
-        // rounding, so a lane's path length does not depend on which one it got).
+        // rounding, so which one a lane gets moves its path length by less than that).
         constexpr float kSeriesX = 0.02f, kShortX = 0.005f;
         const int form = __reduce_max_sync(__activemask(), xabs < kShortX ? 0 : (xabs < kSeriesX ? 1 : 2));
         const bool series = form < 2;
