@@ -37,6 +37,7 @@ ELBM_KERNEL_AUTO, ELBM_KERNEL_DIRECT, ELBM_KERNEL_ROWS = 0, 1, 2
 ELBM_BATCH_GRAPH, ELBM_BATCH_LAUNCHES, ELBM_BATCH_PER_DOMAIN, ELBM_BATCH_PERSISTENT, ELBM_BATCH_AUTO = 0, 1, 2, 3, 4
 ELBM_BRANCH_CUTOFF, ELBM_BRANCH_SOLVED, ELBM_BRANCH_CLAMPED = 0, 1, 2
 ELBM_HIST_BINS = 256
+ELBM_NOALLOC_SCRATCH_BYTES = 4096
 
 STORAGE_NAMES = {"f64": ELBM_STORE_F64, "f32": ELBM_STORE_F32, "f16dev": ELBM_STORE_F16DEV,
                  "bf16dev": ELBM_STORE_BF16DEV}

@@ -145,3 +145,16 @@ def test_batch_create_rejects_bad_arguments(lib, lattice, dims, betas, code):
         E.elbm_batch_create(lattice, dims, betas)
     assert ei.value.code == code
     assert "elbm_batch_create" in E.elbm_batch_last_error(None)
+
+
+def test_binding_constants_match_the_header():
+    """Every #define ELBM_* integer constant of include/elbm.h has the same value in the
+    Python binding (which marshals arguments only and must not drift from the C ABI)."""
+    import re
+
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "elbm.h")).read()
+    defs = dict(re.findall(r"#define\s+(ELBM_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", hdr))
+    assert len(defs) > 20
+    for name, value in defs.items():
+        assert getattr(E, name, None) == int(value), name
