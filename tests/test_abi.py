@@ -158,3 +158,28 @@ def test_binding_constants_match_the_header():
     assert len(defs) > 20
     for name, value in defs.items():
         assert getattr(E, name, None) == int(value), name
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """elbm_opts and elbm_diag as the C compiler lays them out (size and every field's
+    offset) equal the ctypes mirrors the binding passes by pointer."""
+    import subprocess
+
+    structs = {"elbm_opts": E.elbm_opts, "elbm_diag": E.elbm_diag}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "elbm.h"', "int main(void){"]
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines.append("return 0;}")
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    r = subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for sname, cls in structs.items():
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
