@@ -10,6 +10,9 @@ second), and the fused kernel's fraction of the measured HBM bandwidth.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+Defaults: K = 5000 (the length of the Taylor-Green configuration; the step gets
+costlier as the vortex breaks down, so K decides what is measured), W = 20.
+
 N > 1 runs under torch.distributed.run as independent replicas (one full
 domain per GPU; the domain is not split across GPUs) and reports the aggregate.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
