@@ -40,7 +40,9 @@ BETA = 0.999
 U0 = 0.05
 LATTICE_Q = 27
 DIAG_EVERY = 100
+FLOW_STEPS = 5000  # length of the Taylor-Green configuration
 STORAGE = "f32"
+ELEM_BYTES = {"f32": 4, "f32dev": 4, "f16dev": 2, "bf16dev": 2}
 WORKLOAD = "D3Q27 256^3 periodic Taylor-Green vortex, u0=0.05, beta=0.999, FP32 SoA ping-pong"
 METRIC = "MLUPS (D3Q27 256^3 FP32 entropic LBM step)"
 PROFILE = os.path.join(ROOT, "profiles", "k_step_d3q27_f32_tgv256.md")
@@ -179,6 +181,66 @@ class Replicas:
             self.dist.barrier()
             self.dist.destroy_process_group()
             self.dist = None
+
+
+def xmax_bands(d: dict, N: int) -> dict:
+    """Shares of nodes by |x|max of the next collision (the diagnostics' bands)."""
+    names = ["cutoff_lt_1e-3", "short_series_lt_5e-3", "long_series_lt_2e-2", "per_population_ge_2e-2"]
+    return {k: v / N for k, v in zip(names, d["n_xmax_band"])}
+
+
+def e2e_itemised(E, sim, rho_h, u_h, rho_d, u_d, rho_out, u_out, barrier, h2d, d2h, reps: int = 3) -> dict:
+    """The fixed cost of one end-to-end call, by part (median of a few repetitions): the
+    initial state from host arrays and from device arrays (their difference is the
+    host-to-device copy), and the moments into host and into device arrays."""
+    import torch
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            barrier()
+            t0 = time.perf_counter()
+            fn()
+            barrier()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts))
+
+    rho_dd = torch.empty_like(rho_d)
+    u_dd = torch.empty_like(u_d)
+    t_init_h = timed(lambda: E.elbm_init_equilibrium(sim.h, rho_h.numpy(), u_h.numpy(), E.ELBM_MEM_HOST))
+    t_init_d = timed(lambda: E.elbm_init_equilibrium(sim.h, rho_d, u_d, E.ELBM_MEM_DEVICE))
+    t_mom_h = timed(lambda: E.elbm_moments(sim.h, rho_out.numpy(), u_out.numpy(), E.ELBM_MEM_HOST))
+    t_mom_d = timed(lambda: E.elbm_moments(sim.h, rho_dd, u_dd, E.ELBM_MEM_DEVICE))
+    return {"init_from_host_ms": 1e3 * t_init_h, "init_from_device_ms": 1e3 * t_init_d,
+            "moments_to_host_ms": 1e3 * t_mom_h, "moments_to_device_ms": 1e3 * t_mom_d,
+            "h2d_gbs": h2d / max(t_init_h - t_init_d, 1e-9) / 1e9,
+            "d2h_gbs": d2h / max(t_mom_h - t_mom_d, 1e-9) / 1e9,
+            "note": "copy rates from the host-minus-device differences; staging allocated before timing"}
+
+
+def late_flow_leg(E, sim, rho_d, u_d, one_step, barrier, steps: int, stream, N: int) -> dict:
+    """K steps of the benchmark flow ending at step FLOW_STEPS, timed like the main region
+    (per-launch CUDA events on the library's stream; the first of every DIAG_EVERY steps is
+    the fused diagnostics step and is left out of the average)."""
+    import torch
+
+    E.elbm_init_equilibrium(sim.h, rho_d, u_d, E.ELBM_MEM_DEVICE)
+    start_step = FLOW_STEPS - steps
+    sim.step(start_step)
+    d = sim.diagnostics()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(steps):
+        one_step(k, evs[k])
+    b.record(stream)
+    barrier()
+    kern = [x.elapsed_time(y) for k, (x, y) in enumerate(evs) if k % DIAG_EVERY != 0]
+    return {"steps": [start_step, FLOW_STEPS], "kernel_ms_avg": float(np.mean(kern)),
+            "ms_per_step": a.elapsed_time(b) / steps, "mlups": N * steps / (a.elapsed_time(b) / 1e3) / 1e6,
+            "xmax_band_frac": xmax_bands(d, N), "n_solved_frac": d["n_solved"] / N,
+            "alpha_range": [d["alpha_min"], d["alpha_max"]]}
 
 
 def aggregate_mlups(nodes_per_rank: int, steps: int, world: int, max_elapsed_s: float) -> float:
@@ -340,29 +402,49 @@ def run_gpu(args):
                   "nonzero_bins": {"%.5f" % edges[b]: int(hist[1 + b]) for b in nz}}
 
     # End to end through the C ABI with host buffers: initial rho/u uploaded from pinned
-    # host memory, K steps (with the diagnostics cadence), rho/u read back to host.
+    # host memory, K steps (with the diagnostics cadence), rho/u read back to host.  One
+    # untimed round trip first: the library allocates its staging buffer on the first
+    # host-memory call, and that allocation is not part of a step.
     rho_out = torch.empty(N, dtype=torch.float64).pin_memory()
     u_out = torch.empty((3, N), dtype=torch.float64).pin_memory()
+    E.elbm_init_equilibrium(sim.h, rho_h.numpy(), u_h.numpy(), E.ELBM_MEM_HOST)
+    E.elbm_moments(sim.h, rho_out.numpy(), u_out.numpy(), E.ELBM_MEM_HOST)
     barrier()
     t0 = time.perf_counter()
     E.elbm_init_equilibrium(sim.h, rho_h.numpy(), u_h.numpy(), E.ELBM_MEM_HOST)
+    t1 = time.perf_counter()
     for k in range(args.steps):
         one_step(k)
+    t2 = time.perf_counter()
     E.elbm_moments(sim.h, rho_out.numpy(), u_out.numpy(), E.ELBM_MEM_HOST)
     barrier()
-    e2e_t = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    e2e_t = t3 - t0
     e2e_t = rep.max(e2e_t)
+    e2e_phases = {"init_ms": 1e3 * (t1 - t0), "steps_enqueue_ms": 1e3 * (t2 - t1),
+                  "moments_and_drain_ms": 1e3 * (t3 - t2)}
     h2d = (rho_h.numel() + u_h.numel()) * 8
     d2h = (rho_out.numel() + u_out.numel()) * 8
+    fixed = e2e_itemised(E, sim, rho_h, u_h, rho_d, u_d, rho_out, u_out, barrier, h2d, d2h)
+
+    # The same flow late in the configuration: the vortex breaks down and more nodes need
+    # the longer path-length forms, so the step gets costlier.  The state is advanced
+    # (untimed) to step FLOW_STEPS - K and K steps are timed as above.
+    late = None
+    if not args.no_late_flow and args.steps <= FLOW_STEPS // 2:
+        late = late_flow_leg(E, sim, rho_d, u_d, one_step, barrier, args.steps, stream, N)
 
     peak, peak_src = measured_peaks()
-    elem = {"f32": 4, "f16dev": 2, "bf16dev": 2}[args.storage]
+    elem = ELEM_BYTES[args.storage]
     bytes_per_node = 2 * LATTICE_Q * elem
     # AUTO launches the DIRECT kernel (elbm.h)
     kname = ("k_step_rows" if args.kernel == "rows" else "k_step") + f"<{args.storage}> (D3Q27)"
     achieved = bytes_per_node * N / kern_avg / 1e9
     traffic = profiled_traffic() if (args.storage == STORAGE and args.kernel != "rows") else None
     value = aggregate_mlups(N, args.steps, world, elapsed)
+    if late is not None:
+        late["roofline_frac"] = bytes_per_node * N / late["kernel_ms_avg"] * 1e-6 / peak
+        late["achieved_gbs"] = bytes_per_node * N / late["kernel_ms_avg"] * 1e-6
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -378,13 +460,16 @@ def run_gpu(args):
                      "kernel_ms_avg": 1e3 * kern_avg},
         "e2e": {"value": aggregate_mlups(N, args.steps, world, e2e_t), "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                "what": "elbm_init_equilibrium from pinned host rho,u + K steps + elbm_moments to host"},
+                "what": "elbm_init_equilibrium from pinned host rho,u + K steps + elbm_moments to host",
+                "phases": e2e_phases, "fixed_cost_per_call": fixed},
+        "late_flow": late,
         "gpu_launches": gpu_launches,
         "clocks": clk,
         "physics": {"alpha_min": d["alpha_min"], "alpha_max": d["alpha_max"], "alpha_mean": d["alpha_mean"],
                     "n_solved_frac": d["n_solved"] / N, "n_cutoff_frac": d["n_cutoff"] / N,
                     "n_clamped": d["n_clamped"], "n_nonpositive": d["n_nonpositive"],
                     "dH_max": d["dH_max"], "n_dH_positive": d["n_dH_positive"],
+                    "xmax_band_frac": xmax_bands(d, N),
                     "mass": d["mass"], "H": d["H"], "alpha_hist": alpha_hist},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -483,7 +568,7 @@ def run_precision(args):
     rho0, u0 = inputs.shear_layer_2d(X, Y, Ls)
     checkpoints = sorted(int(c) for c in args.checkpoints.split(","))
     fields, rates = {}, {}
-    for storage in ("f64", "f32", "f16dev", "bf16dev"):
+    for storage in ("f64", "f32", "f32dev", "f16dev", "bf16dev"):
         with E.Simulation(E.ELBM_D2Q9, dims, beta, storage=storage) as sim:
             sim.init_equilibrium(rho0, u0)
             done = 0
@@ -506,7 +591,7 @@ def run_precision(args):
             fields[storage] = out
             rates[storage] = Ls * Ls * t_steps / (t_ms / 1e3) / 1e6
     table = {}
-    for storage in ("f32", "f16dev", "bf16dev"):
+    for storage in ("f32", "f32dev", "f16dev", "bf16dev"):
         rows = {}
         for c in checkpoints:
             r64, u64, _ = fields["f64"][c]
@@ -539,13 +624,17 @@ def run_precision(args):
 
 
 def run_storage(args):
-    """Storage forms from the same initial state in FP64, FP32, FP16 and BF16 deviation
-    storage; step time from CUDA events over steps 10..K (K = --storage-steps) and the
-    velocity error of the final state against the FP64 run.  --storage-lattice d3q27:
-    the benchmark flow, D3Q27 L^3 Taylor-Green vortex (u0 = 0.05, beta = 0.999);
-    d2q9: the doubly periodic shear layer (U0 = 0.04, beta = 0.9995) on a
-    --storage-L^2 lattice (4096^2 by default: both FP32 buffers, 1.2 GB each, far
-    above L2, so the step is HBM-bound as in the benchmark)."""
+    """Storage forms from the same initial state in FP64, FP32, FP32, FP16 and BF16
+    deviation storage: step time from CUDA events over the run (steps 10..K, K =
+    --storage-steps; the moments taken at the checkpoints are outside the events) and the
+    velocity error against the FP64 run at each checkpoint (--storage-checkpoints, K by
+    default), with the growth exponent of the error between checkpoints (err ~ t^p: p ~ 1/2
+    for a random walk of rounding errors, ~1 for a bias) and the step count at which each
+    storage's error would cross 1e-3 on that trend.  --storage-lattice d3q27: the benchmark
+    flow, D3Q27 L^3 Taylor-Green vortex (u0 = 0.05, beta = 0.999; L = --L, 256 by
+    default); d2q9: the doubly periodic shear layer (U0 = 0.04, beta = 0.9995) on a
+    --storage-L^2 lattice (4096^2 by default: both FP32 buffers, 1.2 GB each, far above
+    L2, so the step is HBM-bound as in the benchmark)."""
     import torch
 
     from paper_2203_12946_gb300 import elbm as E
@@ -553,10 +642,14 @@ def run_storage(args):
 
     torch.cuda.set_device(0)
     K = args.storage_steps
+    cps = sorted({int(c) for c in (args.storage_checkpoints or str(K)).split(",")} | {K})
+    if cps[0] <= 10:
+        raise SystemExit("checkpoints must exceed 10 steps")
     if args.storage_lattice == "d3q27":
         lat, dims, beta, U = E.ELBM_D3Q27, (L, L, L), BETA, U0
         X, Y, Z = inputs.grid(dims)
         rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=U0)
+        del X, Y, Z
         flow = {"flow": "Taylor-Green vortex", "u0": U0}
     else:
         Ls = args.storage_L
@@ -565,30 +658,44 @@ def run_storage(args):
         rho, u = inputs.shear_layer_2d(ix.ravel(), iy.ravel(), Ls, U0=U)
         flow = {"flow": "doubly periodic shear layer", "U0": U}
     N = int(np.prod(dims))
-    res = {}
-    for st in ("f64", "f32", "f16dev", "bf16dev"):
+    u64 = {}
+    out = {}
+    for st in ("f64", "f32", "f32dev", "f16dev", "bf16dev"):
         with E.Simulation(lat, dims, beta, storage=st) as sim:
             sim.init_equilibrium(rho, u)
             sim.step(10)
             stream = torch.cuda.current_stream()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a.record(stream)
-            sim.step(K - 10)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / (K - 10)
-            _, uu = sim.moments()
-            res[st] = (ms, uu.cpu().numpy())
-    u64 = res["f64"][1]
-    out = {}
-    for st, (ms, uu) in res.items():
-        out[st] = {"ms_per_step": ms, "mlups": N / ms / 1e3,
-                   "u_rel_l2_vs_f64": float(np.linalg.norm(uu - u64) / np.linalg.norm(u64)),
-                   "u_linf_over_u0": float(np.max(np.abs(uu - u64)) / U)}
+            done, ms_total, errs = 10, 0.0, {}
+            for c in cps:
+                torch.cuda.synchronize()
+                a.record(stream)
+                sim.step(c - done)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms_total += a.elapsed_time(b)
+                done = c
+                uu = sim.moments()[1].cpu().numpy()
+                if st == "f64":
+                    u64[c] = uu
+                else:
+                    errs[c] = float(np.linalg.norm(uu - u64[c]) / np.linalg.norm(u64[c]))
+            ms = ms_total / (K - 10)
+        res = {"ms_per_step": ms, "mlups": N / ms / 1e3}
+        if st != "f64":
+            res["u_rel_l2_vs_f64"] = errs[K]
+            res["u_rel_l2_at"] = {str(c): e for c, e in errs.items()}
+            if len(cps) > 1:
+                ts = np.array(cps, dtype=float)
+                es = np.array([errs[c] for c in cps])
+                slope, icpt = np.polyfit(np.log(ts), np.log(es), 1)
+                res["growth_exponent"] = float(slope)
+                res["steps_to_1e-3_on_trend"] = float(np.exp((np.log(1e-3) - icpt) / slope)) if slope > 0 else None
+        out[st] = res
     line = {"metric": f"step time and velocity error vs FP64 per storage, {args.storage_lattice.upper()} "
                       f"{flow['flow']}",
-            "config": {"workload": "storage forms", "dims": list(dims), "beta": beta, **flow, "steps": K},
+            "config": {"workload": "storage forms", "dims": list(dims), "beta": beta, **flow, "steps": K,
+                       "checkpoints": cps},
             "results": out}
     print(json.dumps(line), flush=True)
     return 0
@@ -715,9 +822,13 @@ def main():
     ap.add_argument("--adjoint-L", type=int, default=256)
     ap.add_argument("--fd-dirs", type=int, default=4)
     ap.add_argument("--storage-steps", type=int, default=1000)
+    ap.add_argument("--storage-checkpoints", default=None,
+                    help="comma-separated step counts at which the storage workload compares u with FP64")
     ap.add_argument("--storage-lattice", choices=["d3q27", "d2q9"], default="d3q27")
     ap.add_argument("--storage-L", type=int, default=4096, help="side of the D2Q9 storage workload")
-    ap.add_argument("--storage", choices=["f32", "f16dev", "bf16dev"], default=STORAGE)
+    ap.add_argument("--storage", choices=["f32", "f32dev", "f16dev", "bf16dev"], default=STORAGE)
+    ap.add_argument("--no-late-flow", action="store_true",
+                    help="skip the late-flow leg (steps 5000-K .. 5000 of the same flow)")
     ap.add_argument("--L", type=int, default=L, help="domain side (profiling runs only; "
                     "the benchmark workload is 256)")
     args = ap.parse_args()

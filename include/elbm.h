@@ -64,12 +64,19 @@ extern "C" {
 #define ELBM_BC_PERIODIC 0
 
 /* Storage of the populations.  F64 and F32 store f_i and compute in the same
- * precision.  F16DEV and BF16DEV store the deviation f_i - w_i rho0 in IEEE
- * half or bfloat16 and compute in FP32. */
+ * precision.  F32DEV, F16DEV and BF16DEV store the deviation d_i = f_i - c_i
+ * from the reference c_i = w_i rho0 rounded to FP32 (exactly k_i R with
+ * w_i = k_i 6^-D, k_i a power of two, and R = 6^-D rho0 rounded to FP32), in
+ * IEEE single, half or bfloat16, and compute in FP32.  F32DEV collides on the
+ * deviations themselves, so every rounding of the step (the relaxation and the
+ * store) happens at the scale of d_i instead of w_i, for the same 4 bytes per
+ * population as F32.  elbm_get_populations / elbm_set_populations transfer the
+ * stored values (d_i for the deviation storages). */
 #define ELBM_STORE_F64 0
 #define ELBM_STORE_F32 1
 #define ELBM_STORE_F16DEV 2
 #define ELBM_STORE_BF16DEV 3
+#define ELBM_STORE_F32DEV 4
 
 /* Path-length rule.  HIGHER is the paper's alpha_Higher (default); LOWER the
  * more dissipative alpha_Lower (Sec. III A); LBGK the constant alpha = 2;
@@ -143,6 +150,11 @@ typedef struct elbm_diag {
     int64_t n_nonpositive; /* nodes with a population <= 0 or not finite                */
     int64_t n_dH_positive; /* nodes with H[f*] - H[f] > 1e-6 <f, x^2> (an H-theorem
                               violation beyond the rounding of alpha)                   */
+    int64_t n_xmax_band[4]; /* nodes by |x|max of the next collision (Eq. xdef) in
+                               [0, 1e-3) (the cutoff of Appendix D), [1e-3, 5e-3),
+                               [5e-3, 2e-2) and [2e-2, inf) (where the FP32 path
+                               takes its short series, long series and per-population
+                               forms of the path-length coefficients)                   */
 } elbm_diag;
 
 typedef struct elbm elbm_t;
@@ -387,10 +399,12 @@ int elbm_batch_check_wait_timeout(elbm_batch_t *b);
  * Computes exactly what elbm_diagnostics computes, for a caller-owned device
  * buffer `populations` (Q*N elements of opts->storage, the layout above)
  * holding a post-collision state.  lattice, dims, beta and opts mean what they
- * mean for elbm_create (opts may be NULL: defaults; only storage, alpha_mode,
- * cutoff, b_variant, rho0, device and stream are used; opts->device must be
- * the current device).  *out and alpha_hist (ELBM_HIST_BINS + 2 counts, may be
- * NULL) are host memory.  Synchronises opts->stream.
+ * mean for elbm_create (opts may be NULL: the defaults on the current device
+ * and the legacy default stream; only storage, alpha_mode, cutoff, b_variant,
+ * rho0, device and stream are used; opts->device must be the current device).
+ * populations must be device or managed memory of the current device, aligned
+ * to its storage element.  *out and alpha_hist (ELBM_HIST_BINS + 2 counts, may
+ * be NULL) are host memory.  Synchronises opts->stream.
  *
  * Scratch: the reduction accumulator lives in a file-scope device array of
  * ELBM_NOALLOC_SCRATCH_BYTES bytes, present on every GPU that loads the
@@ -398,13 +412,16 @@ int elbm_batch_check_wait_timeout(elbm_batch_t *b);
  * library routine is called.  A call whose scratch would exceed that maximum
  * is rejected with ELBM_ERR_ARG.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call clears the array
- * before use, but all calls share it: calls that overlap on the GPU (from
- * different streams or host threads) race and must be serialised by the
- * caller.
+ * make that first call before any stream capture.  The address is kept for the
+ * life of the process, so the call is not valid after a cudaDeviceReset of
+ * that device.  Every call clears the array before use, but all calls share
+ * it: calls that overlap on the GPU (from different streams or host threads)
+ * race and must be serialised by the caller.
  *
  * Errors (message in elbm_last_error(NULL)): ELBM_ERR_ARG (null pointer,
- * lattice, dims, beta, options, device not current, scratch too small),
+ * lattice, dims or their product above 2^31 nodes, beta, options, a buffer
+ * that is misaligned or not device memory of the current device, device not
+ * current, scratch too small) -- all decided before any work reaches the GPU;
  * ELBM_ERR_CUDA, ELBM_ERR_NONPHYSICAL (after filling *out). */
 #define ELBM_NOALLOC_SCRATCH_BYTES 4096
 int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], double beta, const elbm_opts *opts,

@@ -63,7 +63,8 @@ size_t storage_size(int storage)
 {
     switch (storage) {
     case ELBM_STORE_F64: return 8;
-    case ELBM_STORE_F32: return 4;
+    case ELBM_STORE_F32:
+    case ELBM_STORE_F32DEV: return 4;
     case ELBM_STORE_F16DEV:
     case ELBM_STORE_BF16DEV: return 2;
     default: return 0;
@@ -79,7 +80,7 @@ CollideParams params_of(const elbm_t *h)
     p.b_variant = h->opts.b_variant;
     p.rho0 = h->opts.rho0;
     p.beta_f = float(p.beta);
-    p.rho0_f = float(p.rho0);
+    p.dunit_f = h->D == 2 ? eelbm::dev_unit<2>(p.rho0) : eelbm::dev_unit<3>(p.rho0);
     for (int a = 0; a < 3; ++a) p.force[a] = h->force[a];
     return p;
 }
@@ -516,6 +517,7 @@ int read_diag_acc(elbm_t *h, elbm_diag *out, int64_t *alpha_hist, const char *wh
     out->n_clamped = int64_t(acc.cnt[2]);
     out->n_nonpositive = int64_t(acc.cnt[3]);
     out->n_dH_positive = int64_t(acc.cnt[4]);
+    for (int b = 0; b < 4; ++b) out->n_xmax_band[b] = int64_t(acc.cnt[5 + b]);
     if (alpha_hist)
         for (int b = 0; b < ELBM_HIST_BINS + 2; ++b) alpha_hist[b] = int64_t(acc.hist[b]);
     if (out->n_nonpositive > 0)

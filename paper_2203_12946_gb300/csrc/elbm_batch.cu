@@ -5,8 +5,9 @@
 // Layout: every domain's populations are one SoA block [Q][N_d] inside a shared
 // pair of buffers, at an element offset rounded up to 256 bytes, so all
 // single-domain kernels (init, moments, diagnostics) run on a domain's block
-// unchanged.  A step is one launch of k_step_batch over a host-built table of
-// work items (domain, y, z, x0); elbm_batch_step can also replay the n launches
+// unchanged.  A step is one launch of k_step_batch per run of up to 64 domains,
+// whose sides, offsets, betas and work-item counts travel in the launch's
+// parameter table (one block per x-row chunk); elbm_batch_step can also replay the n launches
 // as one CUDA graph, advance all n steps in one cooperative launch of
 // k_step_persist (blocks own fixed runs of work items and wait, with bounded
 // spins, only for the other owners of their domains), or launch the
@@ -46,10 +47,8 @@ struct elbm_batch {
     size_t total_elems = 0;   // elements per buffer
     void *pop[2] = {nullptr, nullptr};
     int cur = 0;
-    BatchDomain *d_doms = nullptr;
     int bx = 128;                          // work-item width (autotuned)
-    std::map<int, std::vector<int4>> items; // per width, host copy
-    std::map<int, int4 *> d_items;          // per width, device copy
+    std::map<int, std::vector<eelbm::BatchTable>> tables; // per width: the launches of one batched step
     double *stage = nullptr;
     size_t stage_bytes = 0;
     DiagAcc *acc = nullptr;
@@ -62,6 +61,7 @@ struct elbm_batch {
         int *seg_off = nullptr;
         unsigned *owners = nullptr;
         unsigned *cnt = nullptr;
+        eelbm::BatchTableDom *doms = nullptr; // every domain's entry at this width (device)
         std::vector<unsigned> h_owners; // host copy
         int max_steps = 1;              // steps per launch that keep steps x owners below 2^32
     };
@@ -98,7 +98,8 @@ size_t elem_size(int storage)
 {
     switch (storage) {
     case ELBM_STORE_F64: return 8;
-    case ELBM_STORE_F32: return 4;
+    case ELBM_STORE_F32:
+    case ELBM_STORE_F32DEV: return 4;
     case ELBM_STORE_F16DEV:
     case ELBM_STORE_BF16DEV: return 2;
     default: return 0;
@@ -114,7 +115,7 @@ CollideParams params_of(const elbm_batch_t *b, double beta)
     p.b_variant = b->opts.b_variant;
     p.rho0 = b->opts.rho0;
     p.beta_f = float(p.beta);
-    p.rho0_f = float(p.rho0);
+    p.dunit_f = b->D == 2 ? eelbm::dev_unit<2>(p.rho0) : eelbm::dev_unit<3>(p.rho0);
     return p;
 }
 
@@ -151,39 +152,58 @@ int check_domain(elbm_batch_t *b, int d, const char *what)
     return ELBM_OK;
 }
 
-// Work items of width bx: every x-row of every domain, in chunks of bx nodes.
-int build_items(elbm_batch_t *b, int bx)
+// Parameter tables of the batched launches of width bx: consecutive runs of up to
+// kBatchTableDomains domains, one launch each.
+int build_tables(elbm_batch_t *b, int bx)
 {
-    if (b->d_items.count(bx)) return ELBM_OK;
-    std::vector<int4> it;
-    for (int d = 0; d < int(b->doms.size()); ++d) {
-        const BatchDomain &dm = b->doms[d];
-        for (int z = 0; z < dm.nz; ++z)
-            for (int y = 0; y < dm.ny; ++y)
-                for (int x0 = 0; x0 < dm.nx; x0 += bx) it.push_back(make_int4(d, y, z, x0));
+    if (b->tables.count(bx)) return ELBM_OK;
+    std::vector<eelbm::BatchTable> tabs;
+    const int nd = int(b->doms.size());
+    for (int d0 = 0; d0 < nd; d0 += eelbm::kBatchTableDomains) {
+        eelbm::BatchTable t;
+        memset(&t, 0, sizeof t);
+        t.n = std::min(nd - d0, eelbm::kBatchTableDomains);
+        int64_t items = 0;
+        for (int k = 0; k < t.n; ++k) {
+            const BatchDomain &dm = b->doms[size_t(d0 + k)];
+            eelbm::BatchTableDom &td = t.dom[k];
+            td.nx = dm.nx;
+            td.ny = dm.ny;
+            td.nz = dm.nz;
+            td.xblocks = (dm.nx + bx - 1) / bx;
+            td.off = dm.off;
+            td.beta = dm.beta;
+            td.beta_f = dm.beta_f;
+            t.item0[k] = int(items);
+            items += int64_t(td.xblocks) * dm.ny * dm.nz;
+            if (items > int64_t(0x7fffffff))
+                return bfail(b, ELBM_ERR_ARG, "elbm_batch: too many work items in one launch");
+        }
+        t.item0[t.n] = int(items);
+        t.shift = 0;
+        while (((items - 1) >> t.shift) >= eelbm::kBatchCoarse) ++t.shift;
+        for (int c = 0, d = 0; c < eelbm::kBatchCoarse; ++c) {
+            const int64_t b0 = int64_t(c) << t.shift;
+            while (d + 1 < t.n && t.item0[d + 1] <= b0) ++d;
+            t.coarse[c] = (unsigned char)d;
+        }
+        tabs.push_back(t);
     }
-    if (it.size() > size_t(0x7fffffff))
-        return bfail(b, ELBM_ERR_ARG, "elbm_batch: too many work items (%zu)", it.size());
-    int4 *dev = nullptr;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&dev), it.size() * sizeof(int4));
-    if (e == cudaSuccess) e = cudaMemcpy(dev, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(dev);
-        return bcuda(b, e, "elbm_batch: work-item table");
-    }
-    b->items[bx] = std::move(it);
-    b->d_items[bx] = dev;
+    b->tables[bx] = std::move(tabs);
     return ELBM_OK;
 }
 
 cudaError_t launch_batch(elbm_batch_t *b, const void *fin, void *fout, int bx)
 {
     const CollideParams p = params_of(b, 0.0); // beta comes from the domain table
-    const int n = int(b->items[bx].size());
-    return b->D == 2 ? eelbm::launch_step_batch_d2q9(b->opts.storage, fin, fout, b->d_doms, b->d_items[bx], n, bx,
-                                                      p, b->stream)
-                     : eelbm::launch_step_batch_d3q27(b->opts.storage, fin, fout, b->d_doms, b->d_items[bx], n,
-                                                       bx, p, b->stream);
+    if (build_tables(b, bx) != ELBM_OK) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    for (const eelbm::BatchTable &t : b->tables[bx]) {
+        e = b->D == 2 ? eelbm::launch_step_batch_d2q9(b->opts.storage, fin, fout, t, bx, p, b->stream)
+                      : eelbm::launch_step_batch_d3q27(b->opts.storage, fin, fout, t, bx, p, b->stream);
+        if (e != cudaSuccess) break;
+    }
+    return e;
 }
 
 int ensure_stage(elbm_batch_t *b, size_t bytes)
@@ -214,20 +234,27 @@ void drop_persist(elbm_batch_t *b)
         cudaFree(kv.second.seg_off);
         cudaFree(kv.second.owners);
         cudaFree(kv.second.cnt);
+        cudaFree(kv.second.doms);
     }
     b->persist.clear();
 }
 
 // Static partition of the work items of width bx over every resident block
 // (blocks per SM from the occupancy calculator, times the SM count): block k
-// takes items [k I / G, (k + 1) I / G), cut into one segment per domain it touches.
+// takes items [k I / G, (k + 1) I / G) of the domains' items in order, cut into one
+// segment per domain it touches, numbered inside that domain.
 int build_persist(elbm_batch_t *b, int bx)
 {
     if (b->persist.count(bx)) return ELBM_OK;
-    int st = build_items(b, bx);
+    int st = build_tables(b, bx);
     if (st != ELBM_OK) return st;
-    const std::vector<int4> &it = b->items[bx];
-    const int64_t I = int64_t(it.size());
+    std::vector<eelbm::BatchTableDom> tdoms;
+    for (const eelbm::BatchTable &t : b->tables[bx])
+        for (int k = 0; k < t.n; ++k) tdoms.push_back(t.dom[k]);
+    std::vector<int64_t> first(tdoms.size() + 1, 0); // first global item of each domain
+    for (size_t d = 0; d < tdoms.size(); ++d)
+        first[d + 1] = first[d] + int64_t(tdoms[d].xblocks) * tdoms[d].ny * tdoms[d].nz;
+    const int64_t I = first.back();
     int per_sm = 0;
     cudaError_t e = b->D == 2 ? eelbm::persist_blocks_per_sm_d2q9(b->opts.storage, bx, &per_sm)
                               : eelbm::persist_blocks_per_sm_d3q27(b->opts.storage, bx, &per_sm);
@@ -237,15 +264,15 @@ int build_persist(elbm_batch_t *b, int bx)
     std::vector<int4> segs;
     std::vector<int> seg_off(size_t(G) + 1, 0);
     std::vector<unsigned> owners(b->doms.size(), 0u);
+    size_t d = 0;
     for (int k = 0; k < G; ++k) {
         seg_off[k] = int(segs.size());
         const int64_t w0 = int64_t(k) * I / G, w1 = int64_t(k + 1) * I / G;
         for (int64_t w = w0; w < w1;) {
-            const int d = it[size_t(w)].x;
-            int64_t e1 = w;
-            while (e1 < w1 && it[size_t(e1)].x == d) ++e1;
-            segs.push_back(make_int4(d, int(w), int(e1), 0));
-            owners[size_t(d)] += 1u;
+            while (first[d + 1] <= w) ++d;
+            const int64_t e1 = std::min(w1, first[d + 1]);
+            segs.push_back(make_int4(int(d), int(w - first[d]), int(e1 - first[d]), 0));
+            owners[d] += 1u;
             w = e1;
         }
     }
@@ -255,6 +282,10 @@ int build_persist(elbm_batch_t *b, int bx)
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&ps.seg_off), seg_off.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&ps.owners), owners.size() * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&ps.cnt), owners.size() * sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&ps.doms), tdoms.size() * sizeof(eelbm::BatchTableDom));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ps.doms, tdoms.data(), tdoms.size() * sizeof(eelbm::BatchTableDom), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(ps.segs, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -266,6 +297,7 @@ int build_persist(elbm_batch_t *b, int bx)
         cudaFree(ps.seg_off);
         cudaFree(ps.owners);
         cudaFree(ps.cnt);
+        cudaFree(ps.doms);
         return bcuda(b, e, "elbm_batch: persistent plan");
     }
     ps.plan.grid = G;
@@ -290,12 +322,10 @@ cudaError_t launch_persist(elbm_batch_t *b, int64_t n, int cur)
         const int k = int(std::min<int64_t>(n - done, ps.max_steps)); // counters stay below 2^32
         e = cudaMemsetAsync(ps.cnt, 0, b->doms.size() * sizeof(unsigned), b->stream);
         if (e == cudaSuccess)
-            e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], cur, k, b->d_doms,
-                                                            b->d_items[b->pbx], ps.plan, b->pbx, p, b->err_word,
-                                                            b->stream)
-                          : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], cur, k,
-                                                             b->d_doms, b->d_items[b->pbx], ps.plan, b->pbx, p,
-                                                             b->err_word, b->stream);
+            e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], cur, k, ps.doms,
+                                                            ps.plan, b->pbx, p, b->err_word, b->stream)
+                          : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], cur, k, ps.doms,
+                                                             ps.plan, b->pbx, p, b->err_word, b->stream);
         cur ^= k & 1;
         done += k;
     }
@@ -395,9 +425,6 @@ int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64
     e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, o.device);
     if (e == cudaSuccess) e = cudaMalloc(&b->pop[0], total * es);
     if (e == cudaSuccess) e = cudaMalloc(&b->pop[1], total * es);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_doms), doms.size() * sizeof(BatchDomain));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_doms, doms.data(), doms.size() * sizeof(BatchDomain), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->acc), sizeof(DiagAcc));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->err_word), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->err_word, 0, sizeof(int));
@@ -405,7 +432,7 @@ int elbm_batch_create(elbm_batch_t **out, int lattice, int ndomains, const int64
         elbm_batch_destroy(b);
         return bcuda(nullptr, e, "elbm_batch_create: device allocation");
     }
-    int st = build_items(b, b->bx);
+    int st = build_tables(b, b->bx);
     if (st != ELBM_OK) {
         std::string msg = b->err;
         elbm_batch_destroy(b);
@@ -421,10 +448,8 @@ void elbm_batch_destroy(elbm_batch_t *b)
     DeviceGuard guard(b->opts.device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
-    for (auto &kv : b->d_items) cudaFree(kv.second);
     cudaFree(b->pop[0]);
     cudaFree(b->pop[1]);
-    cudaFree(b->d_doms);
     cudaFree(b->stage);
     cudaFree(b->acc);
     cudaFree(b->err_word);
@@ -569,7 +594,7 @@ int elbm_batch_tune(elbm_batch_t *b, int *chosen, double *ms_per_step)
     int best_bx = b->bx;
     for (int c = 0; c < 3; ++c) {
         const int bx = cands[c];
-        int st = build_items(b, bx);
+        int st = build_tables(b, bx);
         if (st != ELBM_OK) return st;
         // trial steps read the current buffer and write the other one: the state is kept
         const void *fin = b->pop[b->cur];
@@ -745,6 +770,7 @@ int elbm_batch_diagnostics(elbm_batch_t *b, int domain, elbm_diag *out, int64_t 
     out->n_clamped = int64_t(acc.cnt[2]);
     out->n_nonpositive = int64_t(acc.cnt[3]);
     out->n_dH_positive = int64_t(acc.cnt[4]);
+    for (int b = 0; b < 4; ++b) out->n_xmax_band[b] = int64_t(acc.cnt[5 + b]);
     if (alpha_hist)
         for (int k = 0; k < ELBM_HIST_BINS + 2; ++k) alpha_hist[k] = int64_t(acc.hist[k]);
     if (out->n_nonpositive > 0)
@@ -822,11 +848,10 @@ int elbm_batch_check_wait_timeout(elbm_batch_t *b)
         const CollideParams p = params_of(b, 0.0);
         // two steps: step 0 writes the spare buffer, every wait before step 1 expires,
         // so the current buffer (the state) is never written
-        e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2, b->d_doms,
-                                                        b->d_items[b->pbx], plan, b->pbx, p, b->err_word, b->stream)
-                      : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2,
-                                                         b->d_doms, b->d_items[b->pbx], plan, b->pbx, p,
-                                                         b->err_word, b->stream);
+        e = b->D == 2 ? eelbm::launch_step_persist_d2q9(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2, ps.doms,
+                                                        plan, b->pbx, p, b->err_word, b->stream)
+                      : eelbm::launch_step_persist_d3q27(b->opts.storage, b->pop[0], b->pop[1], b->cur, 2, ps.doms,
+                                                         plan, b->pbx, p, b->err_word, b->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     cudaFree(d_ghost);

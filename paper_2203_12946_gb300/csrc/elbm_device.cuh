@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace eelbm {
 
 // ---------------------------------------------------------------------------
@@ -83,22 +85,32 @@ struct CollideParams {
     int b_variant; // 0 = derived denominators (alpha_L beta x), 1 = printed (alpha_L x)
     double rho0;   // reference density of deviation storage
     double force[3] = {0.0, 0.0, 0.0}; // uniform body force (not from the paper), used by the forced kernels
-    float beta_f = 0.0f; // beta and rho0 rounded to FP32 once on the host (the FP32 kernels
-    float rho0_f = 0.0f; // read these and convert nothing from FP64 per thread)
+    float beta_f = 0.0f;  // beta rounded to FP32 once on the host (no FP64 conversion per thread)
+    float dunit_f = 0.0f; // R = W rho0 rounded to FP32: the unit of the deviation references c_i = k_i R
 };
 
-// beta and rho0 in the compute type.
+// beta in the compute type.
 template <class T>
 __device__ __forceinline__ T beta_of(const CollideParams &p)
 {
     if constexpr (sizeof(T) == 4) return p.beta_f;
     else return p.beta;
 }
-template <class T>
-__device__ __forceinline__ T rho0_of(const CollideParams &p)
+
+// Deviation storage keeps d_i = f_i - c_i with the reference c_i = k_i R,
+// R = W rho0 rounded to FP32 (W = 6^-D; w_i = k_i W with k_i a power of two, so
+// c_i is w_i rho0 rounded to FP32, and the same value in every precision).  With
+// the reference exact in FP32, sum_i c_i = 6^D R and rho = 6^D R + sum_i d_i.
+template <int D>
+__host__ __device__ inline float dev_unit(double rho0)
 {
-    if constexpr (sizeof(T) == 4) return p.rho0_f;
-    else return p.rho0;
+    return float(weight_unit(D) * rho0);
+}
+// c_i in the compute type T, from R in FP32.
+template <int D, class T>
+__device__ __forceinline__ T dev_ref(int i, float R)
+{
+    return T(weight_k(D, i)) * T(R);
 }
 
 // ---------------------------------------------------------------------------
@@ -140,56 +152,72 @@ __device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 
 // ---------------------------------------------------------------------------
-// Storage traits.  load/store convert between the stored element and the
-// compute type; deviation storage keeps f_i - w_i rho0.
+// Storage traits.  raw/pack convert between the stored element and the compute
+// type as they are (populations, or deviations d_i = f_i - c_i where kDev);
+// load/store (and load64/store64 for FP64 companions) take the reference c_i of
+// population i and convert to and from populations f_i.  The step kernels
+// collide on the raw values: for deviation storage the collision works on d_i
+// directly (collide_stored), so no rounding happens at the scale of w_i.
 // ---------------------------------------------------------------------------
 struct StoreF64 {
     using S = double;
     using T = double;
+    static constexpr bool kDev = false;
     static constexpr int kRows = 0; // row-staged kernel not instantiated (FP64 is the parity path)
-    __device__ static __forceinline__ T load(S s, T, T) { return s; }
-    __device__ static __forceinline__ S store(T f, T, T) { return f; }
-    __device__ static __forceinline__ double load64(S s, double, double) { return s; }
-    __device__ static __forceinline__ S store64(double f, double, double) { return f; }
+    __device__ static __forceinline__ T raw(S s) { return s; }
+    __device__ static __forceinline__ S pack(T v) { return v; }
+    __device__ static __forceinline__ T load(S s, T) { return s; }
+    __device__ static __forceinline__ S store(T f, T) { return f; }
+    __device__ static __forceinline__ double load64(S s, double) { return s; }
+    __device__ static __forceinline__ S store64(double f, double) { return f; }
 };
 struct StoreF32 {
-    static constexpr int kRows = 1;
     using S = float;
     using T = float;
-    __device__ static __forceinline__ T load(S s, T, T) { return s; }
-    __device__ static __forceinline__ S store(T f, T, T) { return f; }
-    __device__ static __forceinline__ double load64(S s, double, double) { return double(s); }
-    __device__ static __forceinline__ S store64(double f, double, double) { return float(f); }
+    static constexpr bool kDev = false;
+    static constexpr int kRows = 1;
+    __device__ static __forceinline__ T raw(S s) { return s; }
+    __device__ static __forceinline__ S pack(T v) { return v; }
+    __device__ static __forceinline__ T load(S s, T) { return s; }
+    __device__ static __forceinline__ S store(T f, T) { return f; }
+    __device__ static __forceinline__ double load64(S s, double) { return double(s); }
+    __device__ static __forceinline__ S store64(double f, double) { return float(f); }
+};
+struct StoreF32Dev {
+    using S = float;
+    using T = float;
+    static constexpr bool kDev = true;
+    static constexpr int kRows = 1;
+    __device__ static __forceinline__ T raw(S s) { return s; }
+    __device__ static __forceinline__ S pack(T v) { return v; }
+    __device__ static __forceinline__ T load(S s, T c) { return c + s; }
+    __device__ static __forceinline__ S store(T f, T c) { return f - c; }
+    __device__ static __forceinline__ double load64(S s, double c) { return c + double(s); }
+    __device__ static __forceinline__ S store64(double f, double c) { return float(f - c); }
 };
 struct StoreF16Dev {
-    static constexpr int kRows = 1;
     using S = __half;
     using T = float;
-    __device__ static __forceinline__ T load(S s, T w, T rho0) { return fmaf(w, rho0, __half2float(s)); }
-    __device__ static __forceinline__ S store(T f, T w, T rho0) { return __float2half_rn(fmaf(-w, rho0, f)); }
-    __device__ static __forceinline__ double load64(S s, double w, double rho0)
-    {
-        return w * rho0 + double(__half2float(s));
-    }
-    __device__ static __forceinline__ S store64(double f, double w, double rho0)
-    {
-        return __double2half(f - w * rho0);
-    }
+    static constexpr bool kDev = true;
+    static constexpr int kRows = 1;
+    __device__ static __forceinline__ T raw(S s) { return __half2float(s); }
+    __device__ static __forceinline__ S pack(T v) { return __float2half_rn(v); }
+    __device__ static __forceinline__ T load(S s, T c) { return c + raw(s); }
+    __device__ static __forceinline__ S store(T f, T c) { return pack(f - c); }
+    __device__ static __forceinline__ double load64(S s, double c) { return c + double(__half2float(s)); }
+    __device__ static __forceinline__ S store64(double f, double c) { return __double2half(f - c); }
 };
 struct StoreBF16Dev {
-    static constexpr int kRows = 1;
     using S = __nv_bfloat16;
     using T = float;
-    __device__ static __forceinline__ T load(S s, T w, T rho0) { return fmaf(w, rho0, __bfloat162float(s)); }
-    __device__ static __forceinline__ S store(T f, T w, T rho0) { return __float2bfloat16_rn(fmaf(-w, rho0, f)); }
-    __device__ static __forceinline__ double load64(S s, double w, double rho0)
-    {
-        return w * rho0 + double(__bfloat162float(s));
-    }
-    __device__ static __forceinline__ S store64(double f, double w, double rho0)
-    {
-        return __double2bfloat16(f - w * rho0);
-    }
+    static constexpr bool kDev = true;
+    static constexpr int kRows = 1;
+    __device__ static __forceinline__ T raw(S s) { return __bfloat162float(s); }
+    __device__ static __forceinline__ S pack(T v) { return __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ T load(S s, T c) { return c + raw(s); }
+    __device__ static __forceinline__ S store(T f, T c) { return pack(f - c); }
+    __device__ static __forceinline__ double load64(S s, double c) { return c + double(__bfloat162float(s)); }
+    __device__ static __forceinline__ S store64(double f, double c) { return __double2bfloat16(f - c); }
 };
 
 template <class T>
@@ -437,8 +465,18 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
 // padding lane (f = 1, x = 0) that contributes nothing to any sum.  The
 // Omega-/Omega+ restricted sums are taken branch-free with min(x,0) / max(x,0): a
 // term of the other set is exactly zero, so the sums equal the restricted ones.
-//   in : fp[NP]  pre-collision populations, pair layout
-//   out: fp[NP]  post-collision populations (when kRelax)
+// The populations are reached through an accessor pa (pa.get(k): pair k; pa.put(k, v):
+// the post-collision pair k); the kernels pass PairRegs, the pairs held in registers.
+// Deviation form (kDev): the pairs hold d_i until the departures are formed (every
+// difference there is taken at the scale of d_i), then f_i = k_i R + d_i, rounded, for
+// the sums (which need f only to FP32 relative accuracy); the relaxation
+// d*_i = d_i + alpha beta x_i f_i takes d_i again from reload(i), the stored value
+// (a second read of the same element, normally an L1 hit), so the deviation form keeps
+// the register footprint of the population form.
+//   in : pa.get  pre-collision populations (deviations d_i = f_i - k_i R when kDev),
+//                pair layout
+//        reload  (kDev and kRelax) the stored value of population i
+//   out: pa.put  post-collision values of the same kind (when kRelax)
 //        xp[NP]  departures x_i (Eq. xdef), pair layout
 //        returns alpha; *branch receives kBranch*
 // ---------------------------------------------------------------------------
@@ -496,30 +534,80 @@ __host__ __device__ constexpr float kpair(int k, int lane)
     return pair_pop(D, k, lane) >= 0 ? float(weight_k(D, pair_pop(D, k, lane))) : 0.0f;
 }
 
-template <int D, bool kRelax = true>
-__device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], float2 (&xp)[Pairs<D>::NP],
-                                                    const CollideParams &p, int *branch)
+// Populations of the pair layout held in registers.
+template <int NP>
+struct PairRegs {
+    float2 (&a)[NP];
+    __device__ __forceinline__ float2 get(int k) const { return a[k]; }
+    __device__ __forceinline__ void put(int k, float2 v) { a[k] = v; }
+};
+
+// A second read of a stored element for reload(i): an explicit load the compiler may not
+// merge with the first read of the same address (it would otherwise keep all Q values of
+// the first read live in registers through the collision).
+__device__ __forceinline__ float load_again(const float *q)
 {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(q));
+    return v;
+}
+__device__ __forceinline__ double load_again(const double *q)
+{
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(q));
+    return v;
+}
+__device__ __forceinline__ __half load_again(const __half *q)
+{
+    unsigned short v;
+    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(v) : "l"(q));
+    return __ushort_as_half(v);
+}
+__device__ __forceinline__ __nv_bfloat16 load_again(const __nv_bfloat16 *q)
+{
+    unsigned short v;
+    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(v) : "l"(q));
+    return __ushort_as_bfloat16(v);
+}
+
+// Stand-in for kernels that never relax deviation storage.
+struct NoReload {
+    __device__ __forceinline__ float operator()(int) const { return 0.0f; }
+};
+
+template <int D, bool kRelax = true, bool kDev = false, class PA, class RL = NoReload>
+__device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D>::NP], const CollideParams &p,
+                                                    int *branch, const RL &reload = RL{})
+{
+    static_assert(!(kDev && kRelax) || !std::is_same<RL, NoReload>::value,
+                  "the deviation form's relaxation needs the stored values again (reload)");
     constexpr int Q = Lattice<D>::Q;
     constexpr int NP = Pairs<D>::NP;
     constexpr bool kPad = (Q % 2) == 1;
     const float beta = p.beta_f;
+    const float R = p.dunit_f; // deviation form: f_i = k_i R + d_i
 
-    // Deviations d_i = f_i - w_i and the moments (Sec. I), summed along the last
-    // axis first (same grouping as node_collide).
-    float2 dp[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) dp[k] = psub(fp[k], f2(wpair<D>(k, 0), wpair<D>(k, 1)));
-    auto ds = [&](int i) -> float {
-        const int sl = pair_slot(D, i);
-        return (sl & 1) ? dp[sl >> 1].y : dp[sl >> 1].x;
-    };
+    // Deviations and the moments (Sec. I): d_i = f_i - w_i, or the stored d_i = f_i - k_i R.
+    // Sums along the last axis first: per column (the first D-1 components fixed) s0 =
+    // sum of d, s1 = (c_last = +1) - (c_last = -1).  The first Q/3 pairs are mirrored
+    // along the last axis, one per column, and start each column's sums; the rest add
+    // the columns' c_last = 0 populations.
     constexpr int P = Q / 3;
     float s0[P], s1[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-        s0[k] = ds(3 * k) + ds(3 * k + 1) + ds(3 * k + 2);
-        s1[k] = ds(3 * k + 2) - ds(3 * k);
+    for (int k = 0; k < NP; ++k) {
+        const float2 v = pa.get(k);
+        const float2 d = kDev ? v : psub(v, f2(wpair<D>(k, 0), wpair<D>(k, 1)));
+        if (k < P) {
+            s0[k] = d.x + d.y;
+            s1[k] = d.y - d.x;
+        } else {
+#pragma unroll
+            for (int lane = 0; lane < 2; ++lane) {
+                const int i = pair_pop(D, k, lane);
+                if (i >= 0) s0[i / 3] += lane ? d.y : d.x;
+            }
+        }
     }
     float drho, j[D];
     if (D == 2) {
@@ -539,10 +627,20 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         j[1] = ty[0] + ty[1] + ty[2];
         j[D - 1] = tz[0] + tz[1] + tz[2];
     }
-    drho -= float(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, float>())); // as in node_collide
-    const float rho = 1.0f + drho;
+    float rho, r, dr;
+    if constexpr (kDev) {
+        // rho = 6^D R + drho and, as 6^D W = 1, r - R = rho W - R = W drho exactly: the
+        // equilibrium's scale r = R + dr is kept in two parts (dr below)
+        rho = fmaf(float(Q == 9 ? 36 : 216), R, drho);
+        dr = fmaf(drho, float(weight_unit(D)), drho * weight_unit_lo<D, float>());
+        r = R;
+    } else {
+        drho -= float(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, float>())); // as in node_collide
+        rho = 1.0f + drho;
+        r = fmaf(rho, float(weight_unit(D)), rho * weight_unit_lo<D, float>());
+        dr = 0.0f;
+    }
     const float irho = rcp_nr(rho);
-    const float r = fmaf(rho, float(weight_unit(D)), rho * weight_unit_lo<D, float>());
 
     // Per axis eps(c) = Upsilon z^c - 1 (as in node_collide).
     float eps[D][3];
@@ -580,11 +678,22 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const float2 E = E_pair(k);
-        // f^eq - f = (k_i r) E_i + (k_i r - f_i), one rounding (as in node_collide)
-        const float2 kr = pmul(f2(kpair<D>(k, 0), kpair<D>(k, 1)), f2(r));
-        float2 delta = pfma(kr, E, psub(kr, fp[k]));
+        const float2 K = f2(kpair<D>(k, 0), kpair<D>(k, 1));
+        float2 delta;
+        if constexpr (kDev) {
+            // f^eq - f = k_i (R + dr)(1 + E_i) - k_i R - d_i = k_i [R E_i + dr (1 + E_i)] - d_i:
+            // the bracket is rounded at the scale of R E_i, k_i (a power of two) scales it
+            // exactly, and the difference with d_i is rounded once
+            const float2 t = pfma(f2(R), E, pfma(f2(dr), E, f2(dr)));
+            delta = pfma(K, t, psub(f2(0.0f), pa.get(k)));
+        } else {
+            // f^eq - f = (k_i r) E_i + (k_i r - f_i), one rounding (as in node_collide)
+            const float2 kr = pmul(K, f2(r));
+            delta = pfma(kr, E, psub(kr, pa.get(k)));
+        }
         if (kPad && k == NP - 1) delta.y = 0.0f; // padding lane: f = 1, x = 0
-        const float2 xi = pmul(delta, prcp(fp[k]));
+        if constexpr (kDev) pa.put(k, pfma(K, f2(R), pa.get(k))); // f = k_i R + d_i (padding: 0 R + 1)
+        const float2 xi = pmul(delta, prcp(pa.get(k)));
         xp[k] = xi;
         xabs = fmaxf(xabs, fmaxf(fabsf(xi.x), fabsf(xi.y))); // three-input max
         xmin = fminf(xmin, fminf(xi.x, xi.y));
@@ -620,7 +729,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const float2 xi = xp[k];
-                const float2 fx2 = pmul(fp[k], pmul(xi, xi)); // f x^2
+                const float2 fx2 = pmul(pa.get(k), pmul(xi, xi)); // f x^2
                 const float2 q3 = pmul(fx2, xi);
                 M2 = padd(M2, fx2);
                 M3 = padd(M3, q3);
@@ -643,7 +752,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
             for (int k = 0; k < NP; ++k) {
                 const float2 xi = xp[k];
                 const float2 x2 = pmul(xi, xi);
-                const float2 fx2 = pmul(fp[k], x2); // f x^2
+                const float2 fx2 = pmul(pa.get(k), x2); // f x^2
                 const float2 q3 = pmul(fx2, xi);
                 const float2 q5 = pmul(q3, x2);
                 M2 = padd(M2, fx2);
@@ -671,7 +780,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const float2 xi = xp[k];
-                const float2 fx2 = pmul(pmul(fp[k], xi), xi); // f x^2
+                const float2 fx2 = pmul(pmul(pa.get(k), xi), xi); // f x^2
                 const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
                 const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
                 b1 = padd(b1, fx2);
@@ -709,7 +818,7 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
                         const float2 nu = pfma(pfma(f2(19.0f), t, f2(80.0f)), t, f2(80.0f));
                         const float2 de = pfma(pfma(pfma(f2(6.0f), t, f2(44.0f)), t, f2(96.0f)), t, f2(64.0f));
                         // f x^3 on Omega+ (0 elsewhere) times the bracket
-                        bp = pfma(pmul(pmul(fp[k], pmul(pmul(xi, xi), xq)), nu), prcp(de), bp);
+                        bp = pfma(pmul(pmul(pa.get(k), pmul(pmul(xi, xi), xq)), nu), prcp(de), bp);
                     }
                     bsum = bp.x + bp.y;
                 }
@@ -731,10 +840,19 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
         br = kBranchClamped;
     }
     if (kRelax) {
-        // f* = f + alpha beta (f^eq - f) with f^eq - f = x f
+        // f* = f + alpha beta (f^eq - f) with f^eq - f = x f (deviation form:
+        // d* = d + alpha beta x f, rounded at the scale of d)
         const float2 ab = f2(alpha * beta);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) fp[k] = pfma(pmul(ab, xp[k]), fp[k], fp[k]);
+        for (int k = 0; k < NP; ++k) {
+            if constexpr (kDev) {
+                const int i1 = pair_pop(D, k, 1);
+                const float2 d = f2(reload(pair_pop(D, k, 0)), i1 >= 0 ? reload(i1) : 1.0f);
+                pa.put(k, pfma(pmul(ab, xp[k]), pa.get(k), d));
+            } else {
+                pa.put(k, pfma(pmul(ab, xp[k]), pa.get(k), pa.get(k)));
+            }
+        }
     }
     *branch = br;
     return alpha;
@@ -742,16 +860,30 @@ __device__ __forceinline__ float node_collide_pairs(float2 (&fp)[Pairs<D>::NP], 
 
 // ---------------------------------------------------------------------------
 // One node's collision on scalar arrays, whatever the compute type: FP32 goes
-// through the packed-pair routine, FP64 through node_collide.
+// through the packed-pair routine (on deviations d_i = f_i - k_i R when kDev),
+// FP64 through node_collide.  f holds populations (or deviations when kDev) and
+// receives the post-collision values of the same kind.
 // ---------------------------------------------------------------------------
-template <int D, class T, bool kRelax = true>
+template <int D, class T, bool kRelax = true, bool kDev = false, class RL = NoReload>
 __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q], const CollideParams &p,
-                                     int *branch)
+                                     int *branch, const RL &reload = RL{})
 {
     constexpr int Q = Lattice<D>::Q;
     if constexpr (sizeof(T) == 4) {
-        // alpha_Iterate1 (a comparison variant with logarithms) stays on the scalar path
-        if (p.mode == kModeIterate1) return node_collide<D, T, kRelax>(f, x, p, branch);
+        if (p.mode == kModeIterate1) {
+            // alpha_Iterate1 (a comparison variant with logarithms) stays on the scalar
+            // path, which takes populations
+            if constexpr (kDev) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] += dev_ref<D, T>(i, p.dunit_f);
+            }
+            const T alpha = node_collide<D, T, kRelax>(f, x, p, branch);
+            if constexpr (kDev) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] -= dev_ref<D, T>(i, p.dunit_f);
+            }
+            return alpha;
+        }
         constexpr int NP = Pairs<D>::NP;
         float2 fp[NP], xp[NP];
 #pragma unroll
@@ -759,7 +891,8 @@ __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q
             const int i1 = pair_pop(D, k, 1);
             fp[k] = make_float2(f[pair_pop(D, k, 0)], i1 >= 0 ? f[i1] : 1.0f);
         }
-        const float alpha = node_collide_pairs<D, kRelax>(fp, xp, p, branch);
+        PairRegs<NP> pr{fp};
+        const float alpha = node_collide_pairs<D, kRelax, kDev>(pr, xp, p, branch, reload);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int sl = pair_slot(D, i);
@@ -768,17 +901,43 @@ __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q
         }
         return alpha;
     } else {
+        static_assert(!kDev, "deviation storage computes in FP32");
         return node_collide<D, T, kRelax>(f, x, p, branch);
     }
+}
+
+// The collision of a step kernel on the values it loaded with ST::raw: deviations
+// for deviation storage, populations otherwise; stores them back with ST::pack.
+// reload(i) returns the stored value of population i again (ST::raw of the same
+// element), which the deviation form's relaxation reads a second time.
+template <int D, class ST, bool kRelax = true, class RL = NoReload>
+__device__ __forceinline__ typename ST::T collide_stored(typename ST::T (&v)[Lattice<D>::Q],
+                                                         typename ST::T (&x)[Lattice<D>::Q],
+                                                         const CollideParams &p, int *branch,
+                                                         const RL &reload = RL{})
+{
+    return collide<D, typename ST::T, kRelax, ST::kDev>(v, x, p, branch, reload);
 }
 
 // ---------------------------------------------------------------------------
 // Pull streaming (Eq. advection): population i at node (x, y, z) comes from
 // (x - c_ix, y - c_iy, z - c_iz) with periodic wrap.
 // ---------------------------------------------------------------------------
-template <int D, class ST>
+// Element offset of population i pulled into node (x, y, z): i N + source node.
+template <int D>
+__device__ __forceinline__ int64_t pull_offset(const Geometry &g, int x, int y, int z, int i)
+{
+    const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+    const int sx = cx == 1 ? (x == 0 ? g.nx - 1 : x - 1) : (cx == -1 ? (x == g.nx - 1 ? 0 : x + 1) : x);
+    const int sy = cy == 1 ? (y == 0 ? g.ny - 1 : y - 1) : (cy == -1 ? (y == g.ny - 1 ? 0 : y + 1) : y);
+    const int sz = cz == 1 ? (z == 0 ? g.nz - 1 : z - 1) : (cz == -1 ? (z == g.nz - 1 ? 0 : z + 1) : z);
+    return (int64_t)i * g.N + ((int64_t)sz * g.ny + sy) * g.nx + sx;
+}
+
+// f receives populations (ST::load); with kRaw, the stored values as they are (ST::raw).
+template <int D, class ST, bool kRaw = false>
 __device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin, const Geometry &g,
-                                          int x, int y, int z, typename ST::T rho0,
+                                          int x, int y, int z, float R,
                                           typename ST::T (&f)[Lattice<D>::Q])
 {
     using T = typename ST::T;
@@ -794,7 +953,8 @@ __device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin
         const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
         const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
         const int64_t src = ((int64_t)sz * g.ny + sy) * g.nx + sx;
-        f[i] = ST::load(__ldg(fin + (int64_t)i * g.N + src), T(weight(D, i)), rho0);
+        const typename ST::S sv = __ldg(fin + (int64_t)i * g.N + src);
+        f[i] = kRaw ? ST::raw(sv) : ST::load(sv, dev_ref<D, T>(i, R));
     }
 }
 
@@ -810,7 +970,9 @@ __device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin
 // and f^eq(v) - f^eq(u) = k_i r sum_a d_a prod_{b<a} (1 + eps_b(v)) prod_{b>a} (1 + eps_b(u))
 // with the products kept as 1 + (small).
 // ---------------------------------------------------------------------------
-template <int D, class T>
+// f holds populations, or deviations d_i = f_i - k_i R when kDev (the added term is
+// the same for both).
+template <int D, class T, bool kDev = false>
 __device__ __forceinline__ void add_force(T (&f)[Lattice<D>::Q], const CollideParams &p)
 {
     constexpr int Q = Lattice<D>::Q;
@@ -819,13 +981,18 @@ __device__ __forceinline__ void add_force(T (&f)[Lattice<D>::Q], const CollidePa
     for (int a = 0; a < D; ++a) j[a] = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const T di = f[i] - T(weight_k(D, i)) * T(weight_unit(D)); // exact
+        const T di = kDev ? f[i] : f[i] - T(weight_k(D, i)) * T(weight_unit(D)); // exact
         drho += di;
 #pragma unroll
         for (int a = 0; a < D; ++a) j[a] += T(vel(D, i, a)) * di;
     }
-    drho -= T(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, T>()));
-    const T rho = T(1) + drho;
+    T rho;
+    if constexpr (kDev) {
+        rho = fma(T(Q == 9 ? 36 : 216), T(p.dunit_f), drho);
+    } else {
+        drho -= T(double(Q == 9 ? 36 : 216) * double(weight_unit_lo<D, T>()));
+        rho = T(1) + drho;
+    }
     const T irho = T(1) / rho;
     const T r = fma(rho, T(weight_unit(D)), rho * weight_unit_lo<D, T>());
     T eu[D][3], ev[D][3], de[D][3];

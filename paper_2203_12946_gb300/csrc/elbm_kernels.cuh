@@ -77,8 +77,7 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
                                                     CollideParams p)
 {
     using T = typename ST::T;
-    T f[Q], xd[Q];
-    const T rho0 = rho0_of<T>(p);
+    T f[Q], xd[Q]; // the stored values (deviations for deviation storage)
     int br;
     if constexpr (kGrid3D) {
         // 3D grid with Q N < 2^32: element offsets in 32 bits (the source rows of
@@ -91,30 +90,32 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
         const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
         const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
         const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        // element offset of population i pulled into this node
+        auto src = [&](int i) -> uint32_t {
             const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
             const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
             const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
             const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
-            const uint32_t off = uint32_t(i) * N + (sz * ny + sy) * nx + sx;
-            f[i] = ST::load(__ldg(fin + off), T(weight(D, i)), rho0);
-        }
-        collide<D, T, true>(f, xd, p, &br);
-        if constexpr (kForce) add_force<D, T>(f, p);
+            return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
+        };
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = ST::raw(__ldg(fin + src(i)));
+        collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(load_again(fin + src(i))); });
+        if constexpr (kForce) add_force<D, T, ST::kDev>(f, p);
         const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::store(f[i], T(weight(D, i)), rho0));
+        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::pack(f[i]));
     } else {
         const int64_t n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
         if (n >= g.N) return;
         int x, y, z;
         node_coords(n, g, x, y, z);
-        pull_load<D, ST>(fin, g, x, y, z, rho0, f);
-        collide<D, T, true>(f, xd, p, &br);
-        if constexpr (kForce) add_force<D, T>(f, p);
+        pull_load<D, ST, true>(fin, g, x, y, z, p.dunit_f, f);
+        collide_stored<D, ST, true>(f, xd, p, &br,
+                                    [&](int i) { return ST::raw(load_again(fin + pull_offset<D>(g, x, y, z, i))); });
+        if constexpr (kForce) add_force<D, T, ST::kDev>(f, p);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
+        for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::pack(f[i]));
     }
 }
 
@@ -152,8 +153,9 @@ __global__ void __launch_bounds__(kAuxBlock) k_init(const double *__restrict__ r
 #pragma unroll
     for (int a = 0; a < D; ++a) un[a] = u[(int64_t)a * g.N + n];
     equilibrium64(rho ? rho[n] : rho_uniform, un, feq);
+    const double R = double(dev_unit<D>(rho0));
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[(int64_t)i * g.N + n] = ST::store64(feq[i], weight(D, i), rho0);
+    for (int i = 0; i < Q; ++i) f[(int64_t)i * g.N + n] = ST::store64(feq[i], weight_k(D, i) * R);
 }
 
 template <class ST>
@@ -165,9 +167,10 @@ __global__ void __launch_bounds__(kAuxBlock) k_moments(const typename ST::S *__r
     const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
     if (n >= g.N) return;
     double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    const double R = double(dev_unit<D>(rho0));
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const double v = ST::load64(f[(int64_t)i * g.N + n], weight(D, i), rho0);
+        const double v = ST::load64(f[(int64_t)i * g.N + n], weight_k(D, i) * R);
         r += v;
 #pragma unroll
         for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * v;
@@ -194,9 +197,9 @@ __global__ void __launch_bounds__(kStepBlock) k_alpha(const typename ST::S *__re
     int x, y, z;
     node_coords(n, g, x, y, z);
     T f[Q], xd[Q];
-    pull_load<D, ST>(fin, g, x, y, z, rho0_of<T>(p), f);
+    pull_load<D, ST, true>(fin, g, x, y, z, p.dunit_f, f); // stored values, as the step collides them
     int br;
-    const T alpha = collide<D, T, false>(f, xd, p, &br);
+    const T alpha = collide_stored<D, ST, false>(f, xd, p, &br);
     if (alpha_out) alpha_out[n] = double(alpha);
     if (flags) flags[n] = uint8_t(br);
     if (nut_out) nut_out[n] = (1.0 / 3.0) * (2.0 - double(alpha)) / (2.0 * double(alpha) * p.beta);
@@ -245,7 +248,7 @@ __device__ __forceinline__ unsigned long long warp_min(unsigned long long v)
 template <class T>
 struct DiagThread {
     double sum[6] = {0, 0, 0, 0, 0, 0};
-    unsigned long long cnt[5] = {0, 0, 0, 0, 0};
+    unsigned long long cnt[kDiagCounts] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long dmax = 0ULL, amin = ~0ULL, amax = 0ULL;
     T p_dr = T(0), p_j[3] = {T(0), T(0), T(0)}, p_h = T(0), p_al = T(0);
     T p_dmax = -INFINITY, p_amin = INFINITY, p_amax = -INFINITY;
@@ -331,6 +334,8 @@ struct DiagThread {
             p_hnodes += 1;
             p_dmax = fmax(p_dmax, dH);
             if (dH > T(1e-6) * s3 && s3 > T(0)) cnt[4] += 1;
+            // |x|max band: the cutoff of Appendix D, then the FP32 coefficient forms
+            cnt[xa < T(1e-3) ? 5 : (xa < T(5e-3) ? 6 : (xa < T(2e-2) ? 7 : 8))] += 1;
         }
         p_al += alpha_t - T(2);
         cnt[br == kBranchCutoff ? 0 : (br == kBranchSolved ? 1 : 2)] += 1;
@@ -354,10 +359,10 @@ __device__ __forceinline__ void diag_finish(DiagThread<T> &dt, DiagAcc *__restri
 {
     constexpr int kWarps = NT / 32;
     __shared__ double s_sum[kWarps][6];
-    __shared__ unsigned long long s_cnt[kWarps][5];
+    __shared__ unsigned long long s_cnt[kWarps][kDiagCounts];
     __shared__ unsigned long long s_ext[kWarps][3];
     double (&sum)[6] = dt.sum;
-    unsigned long long (&cnt)[5] = dt.cnt;
+    unsigned long long (&cnt)[kDiagCounts] = dt.cnt;
     unsigned long long &dmax = dt.dmax, &amin = dt.amin, &amax = dt.amax;
     const T &p_dr = dt.p_dr, &p_h = dt.p_h, &p_al = dt.p_al;
     const T(&p_j)[3] = dt.p_j;
@@ -381,13 +386,13 @@ __device__ __forceinline__ void diag_finish(DiagThread<T> &dt, DiagAcc *__restri
 #pragma unroll
     for (int k = 0; k < 6; ++k) sum[k] = warp_sum(sum[k]);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) cnt[k] = warp_sum(cnt[k]);
+    for (int k = 0; k < kDiagCounts; ++k) cnt[k] = warp_sum(cnt[k]);
     dmax = warp_max(dmax);
     amin = warp_min(amin);
     amax = warp_max(amax);
     if (lane == 0) {
         for (int k = 0; k < 6; ++k) s_sum[warp][k] = sum[k];
-        for (int k = 0; k < 5; ++k) s_cnt[warp][k] = cnt[k];
+        for (int k = 0; k < kDiagCounts; ++k) s_cnt[warp][k] = cnt[k];
         s_ext[warp][0] = dmax;
         s_ext[warp][1] = amin;
         s_ext[warp][2] = amax;
@@ -397,7 +402,7 @@ __device__ __forceinline__ void diag_finish(DiagThread<T> &dt, DiagAcc *__restri
         double v = 0.0;
         for (int w = 0; w < kWarps; ++w) v += s_sum[w][threadIdx.x];
         atomicAdd(&acc->sum[threadIdx.x], v);
-    } else if (threadIdx.x >= 32 && threadIdx.x < 37) {
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + kDiagCounts) {
         const int k = threadIdx.x - 32;
         unsigned long long v = 0;
         for (int w = 0; w < kWarps; ++w) v += s_cnt[w][k];
@@ -432,11 +437,11 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         int x, y, z;
         node_coords(n, g, x, y, z);
         T f[Q], xd[Q], fc[Q];
-        pull_load<D, ST>(fin, g, x, y, z, rho0_of<T>(p), f);
+        pull_load<D, ST, true>(fin, g, x, y, z, p.dunit_f, f); // stored values, as the step collides them
 #pragma unroll
-        for (int i = 0; i < Q; ++i) fc[i] = f[i];
+        for (int i = 0; i < Q; ++i) fc[i] = ST::kDev ? f[i] + dev_ref<D, T>(i, p.dunit_f) : f[i]; // populations
         int br;
-        const T alpha_t = collide<D, T, false>(f, xd, p, &br);
+        const T alpha_t = collide_stored<D, ST, false>(f, xd, p, &br);
         dt.node(fc, xd, alpha_t, br, p, s_hist);
     }
     diag_finish<kAuxBlock>(dt, acc, s_hist);
@@ -463,7 +468,6 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
     for (int b = threadIdx.x; b < ELBM_HIST_BINS + 2; b += kStepBlock) s_hist[b] = 0u;
     __syncthreads();
     DiagThread<T> dt;
-    const T rho0 = rho0_of<T>(p);
     const uint32_t nx = uint32_t(g.nx), ny = uint32_t(g.ny), nz = uint32_t(g.nz), N = uint32_t(g.N);
     const uint32_t xblocks = (nx + kStepBlock - 1) / kStepBlock;
     const uint32_t items = xblocks * ny * nz;
@@ -476,59 +480,81 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
         const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
         const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
         T f[Q], xd[Q], fc[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        auto src = [&](int i) -> uint32_t {
             const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
             const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
             const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
             const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
-            f[i] = ST::load(__ldg(fin + (uint32_t(i) * N + (sz * ny + sy) * nx + sx)), T(weight(D, i)), rho0);
-            fc[i] = f[i];
+            return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
+        };
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f[i] = ST::raw(__ldg(fin + src(i)));
+            fc[i] = ST::kDev ? f[i] + dev_ref<D, T>(i, p.dunit_f) : f[i]; // populations
         }
         int br;
-        const T alpha_t = collide<D, T, true>(f, xd, p, &br);
+        const T alpha_t = collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(load_again(fin + src(i))); });
         dt.node(fc, xd, alpha_t, br, p, s_hist);
         const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::store(f[i], T(weight(D, i)), rho0));
+        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::pack(f[i]));
     }
     diag_finish<kStepBlock>(dt, acc, s_hist);
 }
 
 // --------------------------------------------------------------------------
-// Batched ensemble: one launch advances every domain of the batch.  Work item
-// (domain, y, z, x0) covers nodes x0 .. x0 + BX - 1 of one x-row; the item
-// table is built on the host, so the kernel does no index division.  Each
-// domain has its own beta; everything else is the single-domain step.
+// Batched ensemble: one launch advances up to kBatchTableDomains domains.  Block
+// b is one work item, nodes x0 .. x0 + BX - 1 of one x-row of one domain; the
+// block finds its domain in the launch's parameter table (a coarse index, then a
+// forward scan over the item counts) and its row by division, both uniform over the block,
+// so each thread then addresses its populations as k_step does (32-bit offsets
+// inside the domain).  Each domain has its own beta; everything else is the
+// single-domain step.
 // --------------------------------------------------------------------------
 template <class ST, int BX>
 __global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restrict__ fin,
                                                   typename ST::S *__restrict__ fout,
-                                                  const BatchDomain *__restrict__ doms,
-                                                  const int4 *__restrict__ items, CollideParams p)
+                                                  const __grid_constant__ BatchTable tab, CollideParams p)
 {
     using T = typename ST::T;
-    const int4 it = __ldg(items + blockIdx.x);
-    const BatchDomain dm = doms[it.x];
-    const int x = it.w + int(threadIdx.x);
-    if (x >= dm.nx) return;
-    const Geometry g{dm.nx, dm.ny, dm.nz, dm.N};
+    const int bid = int(blockIdx.x);
+    int lo = tab.coarse[bid >> tab.shift]; // item0[lo] <= bid
+    while (tab.item0[lo + 1] <= bid) ++lo;
+    const BatchTableDom &dm = tab.dom[lo];
+    const uint32_t nx = uint32_t(dm.nx), ny = uint32_t(dm.ny), nz = uint32_t(dm.nz), xb = uint32_t(dm.xblocks);
+    const uint32_t it = uint32_t(bid - tab.item0[lo]);
+    const uint32_t row = it / xb;
+    const uint32_t x = (it - row * xb) * BX + threadIdx.x;
+    if (x >= nx) return;
+    const uint32_t z = row / ny, y = row - z * ny, N = nx * ny * nz;
     p.beta = dm.beta;
     p.beta_f = dm.beta_f;
-    const int64_t n = ((int64_t)it.z * dm.ny + it.y) * dm.nx + x;
-    T f[Q], xd[Q];
-    const T rho0 = rho0_of<T>(p);
-    pull_load<D, ST>(fin + dm.off, g, x, it.y, it.z, rho0, f);
-    int br;
-    collide<D, T, true>(f, xd, p, &br);
+    const typename ST::S *in = fin + dm.off;
     typename ST::S *out = fout + dm.off;
+    const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    T f[Q], xd[Q];
+    auto src = [&](int i) -> uint32_t {
+        const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+        const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+        const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+        const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+        return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
+    };
 #pragma unroll
-    for (int i = 0; i < Q; ++i) __stcs(out + (int64_t)i * g.N + n, ST::store(f[i], T(weight(D, i)), rho0));
+    for (int i = 0; i < Q; ++i) f[i] = ST::raw(__ldg(in + src(i)));
+    int br;
+    collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(load_again(in + src(i))); });
+    const uint32_t n = (z * ny + y) * nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) __stcs(out + (uint32_t(i) * N + n), ST::pack(f[i]));
 }
 
 // --------------------------------------------------------------------------
 // Persistent ensemble: one cooperative launch advances every domain by nsteps.
-// Block b owns a fixed run of work items (plan.segs, balanced on the host) and
+// Block b owns a fixed run of work items (plan.segs, balanced on the host; items
+// numbered inside their domain, located by division as in k_step_batch) and
 // steps it nsteps times.  Domains are independent, so a block waits only for the
 // other owners of the same domain: before step t on domain d, until cnt[d] has
 // counted t steps of each of its owners (release: stores, barrier, fence, atomic
@@ -553,14 +579,12 @@ __device__ __forceinline__ bool wait_count(const unsigned *cnt, unsigned target,
 
 template <class ST, int BX>
 __global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typename ST::S *pop1, int cur,
-                                                    int nsteps, const BatchDomain *__restrict__ doms,
-                                                    const int4 *__restrict__ items, PersistPlan plan,
-                                                    CollideParams p, int *err)
+                                                    int nsteps, const BatchTableDom *__restrict__ doms,
+                                                    PersistPlan plan, CollideParams p, int *err)
 {
     using T = typename ST::T;
     using S = typename ST::S;
     __shared__ int s_ok;
-    const T rho0 = rho0_of<T>(p);
     const int s0 = plan.seg_off[blockIdx.x], s1 = plan.seg_off[blockIdx.x + 1];
     for (int t = 0; t < nsteps; ++t) {
         const bool odd = ((cur + t) & 1) != 0;
@@ -577,34 +601,37 @@ __global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typen
                 __syncthreads();
                 if (!s_ok) return;
             }
-            const BatchDomain dm = doms[seg.x];
+            const BatchTableDom dm = doms[seg.x];
             p.beta = dm.beta;
             p.beta_f = dm.beta_f;
-            const uint32_t nx = uint32_t(dm.nx), ny = uint32_t(dm.ny), nz = uint32_t(dm.nz), N = uint32_t(dm.N);
+            const uint32_t nx = uint32_t(dm.nx), ny = uint32_t(dm.ny), nz = uint32_t(dm.nz), N = nx * ny * nz;
+            const uint32_t xb = uint32_t(dm.xblocks);
             const S *in = fin + dm.off;
             S *out = fout + dm.off;
-            for (int w = seg.y; w < seg.z; ++w) {
-                const int4 it = __ldg(items + w);
-                const uint32_t x = uint32_t(it.w) + threadIdx.x;
+            // the segment's work items, numbered inside the domain: row-major (z, y), x-chunk
+            for (uint32_t w = uint32_t(seg.y); w < uint32_t(seg.z); ++w) {
+                const uint32_t row = w / xb;
+                const uint32_t x = (w - row * xb) * BX + threadIdx.x;
                 if (x >= nx) continue;
-                const uint32_t y = uint32_t(it.y), z = uint32_t(it.z);
+                const uint32_t z = row / ny, y = row - z * ny;
                 const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
                 const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
                 const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
                 T f[Q], xd[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
+                auto src = [&](int i) -> uint32_t {
                     const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
                     const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
                     const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
                     const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
-                    f[i] = ST::load(in[uint32_t(i) * N + (sz * ny + sy) * nx + sx], T(weight(D, i)), rho0);
-                }
+                    return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
+                };
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] = ST::raw(in[src(i)]);
                 int br;
-                collide<D, T, true>(f, xd, p, &br);
+                collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(in[src(i)]); });
                 const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) out[uint32_t(i) * N + n] = ST::store(f[i], T(weight(D, i)), rho0);
+                for (int i = 0; i < Q; ++i) out[uint32_t(i) * N + n] = ST::pack(f[i]);
             }
             __syncthreads(); // every store of this segment issued
             if (threadIdx.x == 0) {
@@ -635,7 +662,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_step_adjoint(const typename ST::S
         int x, y, z;
         node_coords(n, g, x, y, z);
         T F[Q], gl[Q], h[Q];
-        pull_load<D, ST>(fin, g, x, y, z, rho0_of<T>(p), F);
+        pull_load<D, ST>(fin, g, x, y, z, p.dunit_f, F);
 #pragma unroll
         for (int i = 0; i < Q; ++i) gl[i] = gnext[(int64_t)i * g.N + n];
         node_vjp<D, T, kForce>(F, gl, p, h, dfl);
@@ -678,12 +705,13 @@ __global__ void __launch_bounds__(kAuxBlock) k_kinetic_energy(const typename ST:
 {
     using T = typename ST::T;
     double e = 0.0;
+    const double R = double(dev_unit<D>(rho0));
     for (int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; n < g.N; n += (int64_t)gridDim.x * kAuxBlock) {
         double r = 0.0, j[3] = {0.0, 0.0, 0.0};
         double fv[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            fv[i] = ST::load64(f[(int64_t)i * g.N + n], weight(D, i), rho0);
+            fv[i] = ST::load64(f[(int64_t)i * g.N + n], weight_k(D, i) * R);
             r += fv[i];
 #pragma unroll
             for (int a = 0; a < D; ++a) j[a] += vel(D, i, a) * fv[i];
@@ -758,6 +786,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_equilibrium_vjp(const double *__r
     switch (storage) {                                                                         \
     case ELBM_STORE_F64: { using ST = StoreF64; CALL; break; }                                 \
     case ELBM_STORE_F32: { using ST = StoreF32; CALL; break; }                                 \
+    case ELBM_STORE_F32DEV: { using ST = StoreF32Dev; CALL; break; }                           \
     case ELBM_STORE_F16DEV: { using ST = StoreF16Dev; CALL; break; }                           \
     case ELBM_STORE_BF16DEV: { using ST = StoreBF16Dev; CALL; break; }                         \
     default: return cudaErrorInvalidValue;                                                     \
@@ -824,6 +853,7 @@ bool ELBM_CAT(rows_kernel_applies, ELBM_SUFFIX)(int storage, const Geometry &g)
     using namespace ELBM_SUFFIX;
     switch (storage) {
     case ELBM_STORE_F32: return rows_nxmax<StoreF32>(g) > 0;
+    case ELBM_STORE_F32DEV: return rows_nxmax<StoreF32Dev>(g) > 0;
     case ELBM_STORE_F16DEV: return rows_nxmax<StoreF16Dev>(g) > 0;
     case ELBM_STORE_BF16DEV: return rows_nxmax<StoreBF16Dev>(g) > 0;
     default: return false;
@@ -853,6 +883,7 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
     }
         switch (storage) {
         case ELBM_STORE_F32: ELBM_ROWS_FOR(StoreF32) break;
+        case ELBM_STORE_F32DEV: ELBM_ROWS_FOR(StoreF32Dev) break;
         case ELBM_STORE_F16DEV: ELBM_ROWS_FOR(StoreF16Dev) break;
         case ELBM_STORE_BF16DEV: ELBM_ROWS_FOR(StoreBF16Dev) break;
         default: break;
@@ -904,15 +935,16 @@ cudaError_t ELBM_CAT(launch_step_diag, ELBM_SUFFIX)(int storage, const void *fin
 }
 
 cudaError_t ELBM_CAT(launch_step_batch, ELBM_SUFFIX)(int storage, const void *fin, void *fout,
-                                                     const BatchDomain *doms, const int4 *items, int nitems,
-                                                     int bx, const CollideParams &p, cudaStream_t s)
+                                                     const BatchTable &tab, int bx, const CollideParams &p,
+                                                     cudaStream_t s)
 {
     using namespace ELBM_SUFFIX;
-    if (nitems <= 0) return cudaSuccess;
+    const int nitems = tab.item0[tab.n];
+    if (tab.n <= 0 || nitems <= 0) return cudaSuccess;
 #define ELBM_BATCH_BX(BXV)                                                                             \
     ELBM_STORAGE_SWITCH(storage, (k_step_batch<ST, BXV><<<unsigned(nitems), BXV, 0, s>>>(               \
                                      static_cast<const typename ST::S *>(fin),                          \
-                                     static_cast<typename ST::S *>(fout), doms, items, p)))
+                                     static_cast<typename ST::S *>(fout), tab, p)))
     switch (bx) {
     case 64: ELBM_BATCH_BX(64); break;
     case 128: ELBM_BATCH_BX(128); break;
@@ -941,9 +973,8 @@ cudaError_t ELBM_CAT(persist_blocks_per_sm, ELBM_SUFFIX)(int storage, int bx, in
 }
 
 cudaError_t ELBM_CAT(launch_step_persist, ELBM_SUFFIX)(int storage, void *pop0, void *pop1, int cur, int nsteps,
-                                                       const BatchDomain *doms, const int4 *items,
-                                                       const PersistPlan &plan, int bx, const CollideParams &p,
-                                                       int *err, cudaStream_t s)
+                                                       const BatchTableDom *doms, const PersistPlan &plan, int bx,
+                                                       const CollideParams &p, int *err, cudaStream_t s)
 {
     using namespace ELBM_SUFFIX;
     if (nsteps <= 0 || plan.grid <= 0) return cudaSuccess;
@@ -961,7 +992,7 @@ cudaError_t ELBM_CAT(launch_step_persist, ELBM_SUFFIX)(int storage, void *pop0, 
     ELBM_STORAGE_SWITCH(storage, return cudaLaunchKernelEx(&cfg, k_step_persist<ST, BXV>,               \
                                                            static_cast<typename ST::S *>(pop0),        \
                                                            static_cast<typename ST::S *>(pop1), cur,   \
-                                                           nsteps, doms, items, plan, p, err))
+                                                           nsteps, doms, plan, p, err))
     switch (bx) {
     case 64: ELBM_PERSIST_BX(64); break;
     case 128: ELBM_PERSIST_BX(128); break;

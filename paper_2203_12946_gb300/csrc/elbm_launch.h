@@ -23,10 +23,35 @@ struct BatchDomain {
     double beta;
 };
 
+// The domains one batched launch advances, passed by value in the kernel's parameter
+// space (a __grid_constant__ argument): domain d's work items -- x-row chunks of the
+// launch's width, row-major over (z, y), then x -- are blocks item0[d] .. item0[d+1]-1.
+// coarse[b >> shift] is the domain of block (b >> shift) << shift, so a block finds its
+// domain with one table read and a short forward scan.  Every thread of a block finds
+// the same domain, so the lookup and the row arithmetic are uniform; offsets inside a
+// domain are 32-bit (Q N_d < 2^32, checked on creation).
+constexpr int kBatchTableDomains = 64;
+constexpr int kBatchCoarse = 1024;
+struct BatchTableDom {
+    int nx, ny, nz, xblocks; // sides, and x-chunks per row
+    long long off;           // element offset of the domain's SoA block
+    double beta;
+    float beta_f;
+    int pad;
+};
+struct BatchTable {
+    int n;     // domains in the table
+    int shift; // blocks per coarse entry = 2^shift
+    int item0[kBatchTableDomains + 1];
+    BatchTableDom dom[kBatchTableDomains];
+    unsigned char coarse[kBatchCoarse];
+};
+
 // Static partition of one persistent ensemble launch (device arrays): block b
 // steps the work items of segments seg_off[b] .. seg_off[b+1]-1, each segment
-// {domain, first item, end item, 0} inside one domain; owners[d] blocks hold a
-// segment of domain d, and cnt[d] counts their finished (block, step) pairs.
+// {domain, first item, end item, 0} inside one domain (items numbered within the
+// domain); owners[d] blocks hold a segment of domain d, and cnt[d] counts their
+// finished (block, step) pairs.
 struct PersistPlan {
     int grid = 0;
     const int4 *segs = nullptr;
@@ -36,9 +61,12 @@ struct PersistPlan {
 };
 
 // Device-side accumulator of the diagnostics reduction (library scratch).
+constexpr int kDiagCounts = 9;
 struct DiagAcc {
-    double sum[6];                 // mass, momentum x/y/z, H, sum of alpha
-    unsigned long long cnt[5];     // cutoff, solved, clamped, nonpositive, dH-positive
+    double sum[6]; // mass, momentum x/y/z, H, sum of alpha
+    // cutoff, solved, clamped, nonpositive, dH-positive, then |x|max in
+    // [0, 1e-3), [1e-3, 5e-3), [5e-3, 2e-2), [2e-2, inf)
+    unsigned long long cnt[kDiagCounts];
     unsigned long long dH_max_ord; // order-preserving encodings of doubles
     unsigned long long amin_ord;
     unsigned long long amax_ord;
@@ -81,12 +109,12 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
                                           const CollideParams &p, DiagAcc *acc, int num_sms,            \
                                           cudaStream_t s);                                              \
     cudaError_t launch_step_batch_##SUFFIX(int storage, const void *fin, void *fout,                \
-                                           const BatchDomain *doms, const int4 *items, int nitems,   \
-                                           int bx, const CollideParams &p, cudaStream_t s);          \
+                                           const BatchTable &tab, int bx, const CollideParams &p,    \
+                                           cudaStream_t s);                                          \
     cudaError_t launch_step_persist_##SUFFIX(int storage, void *pop0, void *pop1, int cur, int nsteps,  \
-                                             const BatchDomain *doms, const int4 *items,             \
-                                             const PersistPlan &plan, int bx, const CollideParams &p, \
-                                             int *err, cudaStream_t s);                              \
+                                             const BatchTableDom *doms, const PersistPlan &plan,     \
+                                             int bx, const CollideParams &p, int *err,               \
+                                             cudaStream_t s);                                        \
     cudaError_t persist_blocks_per_sm_##SUFFIX(int storage, int bx, int *blocks);                   \
     cudaError_t launch_step_adjoint_##SUFFIX(int storage, const void *fin, const void *gnext,       \
                                              void *gout, const Geometry &g, const CollideParams &p,  \

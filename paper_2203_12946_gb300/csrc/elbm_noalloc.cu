@@ -13,7 +13,10 @@
 // The array is allocated on every GPU that loads the library and lives until
 // the process exits.  All calls share it; each call clears it first, and
 // calls that overlap on the GPU (different streams, or host threads issuing
-// concurrently) race on it and must be serialised by the caller.
+// concurrently) race on it and must be serialised by the caller.  The array's
+// device address is looked up once per device and kept; a cudaDeviceReset
+// destroys the context it belongs to, so the call is not valid after one in the
+// same process.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -71,15 +74,30 @@ extern "C" int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], doub
                                 (long long)dims[a]);
     if (lattice == ELBM_D2Q9 && dims[2] != 1)
         return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: D2Q9 needs dims[2] == 1");
-    if (dims[0] * dims[1] * dims[2] > (int64_t(1) << 31))
+    // the node count in 128 bits: each side may reach 2^30, and their product must not
+    // wrap around in 64 bits before it is compared
+    const unsigned __int128 nodes = (unsigned __int128)dims[0] * (unsigned __int128)dims[1] * (unsigned __int128)dims[2];
+    if (nodes > ((unsigned __int128)1 << 31))
         return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: more than 2^31 nodes");
     if (!(beta > 0.0 && beta < 1.0))
         return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: beta must lie in (0, 1), got %g", beta);
     elbm_opts o;
     elbm_default_opts(&o);
     if (opts) o = *opts;
-    if (o.storage < ELBM_STORE_F64 || o.storage > ELBM_STORE_BF16DEV)
-        return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: unknown storage %d", o.storage);
+    size_t elem = 0;
+    switch (o.storage) {
+    case ELBM_STORE_F64: elem = 8; break;
+    case ELBM_STORE_F32:
+    case ELBM_STORE_F32DEV: elem = 4; break;
+    case ELBM_STORE_F16DEV:
+    case ELBM_STORE_BF16DEV: elem = 2; break;
+    default: return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: unknown storage %d", o.storage);
+    }
+    // the buffer does not come from the library: a pointer that is not aligned to its
+    // element would make the kernel's loads fault
+    if (reinterpret_cast<uintptr_t>(populations) % elem != 0)
+        return noalloc_fail(ELBM_ERR_ARG,
+                            "elbm_diagnostics_noalloc: populations is not aligned to its %zu-byte element", elem);
     if (o.alpha_mode < ELBM_ALPHA_HIGHER || o.alpha_mode > ELBM_ALPHA_ITERATE1 || (o.cutoff != 0 && o.cutoff != 1) ||
         (o.b_variant != ELBM_B_DERIVED && o.b_variant != ELBM_B_PRINTED) || !(o.rho0 > 0.0))
         return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: invalid options");
@@ -94,6 +112,7 @@ extern "C" int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], doub
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(ELBM_ERR_CUDA, "elbm_diagnostics_noalloc: cudaGetDevice: %s",
                                               cudaGetErrorString(e));
+    if (!opts) o.device = dev; // no options: the current device
     if (dev != o.device) {
         return noalloc_fail(ELBM_ERR_ARG,
                             "elbm_diagnostics_noalloc: opts->device = %d but device %d is current; make the "
@@ -102,6 +121,19 @@ extern "C" int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], doub
     }
     if (dev < 0 || dev >= kMaxDevices)
         return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: device ordinal %d not supported", dev);
+    // the buffer must be device (or managed) memory of the current device; the query
+    // allocates nothing
+    cudaPointerAttributes attr;
+    e = cudaPointerGetAttributes(&attr, populations);
+    if (e != cudaSuccess) {
+        cudaGetLastError(); // the failed query leaves no error behind for later calls
+        return noalloc_fail(ELBM_ERR_ARG, "elbm_diagnostics_noalloc: populations is not a CUDA pointer (%s)",
+                            cudaGetErrorString(e));
+    }
+    if ((attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) || attr.device != dev)
+        return noalloc_fail(ELBM_ERR_ARG,
+                            "elbm_diagnostics_noalloc: populations is not device memory of the current device %d",
+                            dev);
 
     // Set-up once per device, with that device current: the device address of
     // the scratch array (its host-side name is only a stand-in) and the SM count.
@@ -147,7 +179,7 @@ extern "C" int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], doub
     p.b_variant = o.b_variant;
     p.rho0 = o.rho0;
     p.beta_f = float(p.beta);
-    p.rho0_f = float(p.rho0);
+    p.dunit_f = lattice == ELBM_D2Q9 ? eelbm::dev_unit<2>(p.rho0) : eelbm::dev_unit<3>(p.rho0);
     e = lattice == ELBM_D2Q9 ? eelbm::launch_diag_d2q9(o.storage, populations, g, p, acc, setup.num_sms, stream)
                              : eelbm::launch_diag_d3q27(o.storage, populations, g, p, acc, setup.num_sms, stream);
     if (e != cudaSuccess)
@@ -174,6 +206,7 @@ extern "C" int elbm_diagnostics_noalloc(int lattice, const int64_t dims[3], doub
     out->n_clamped = int64_t(host.cnt[2]);
     out->n_nonpositive = int64_t(host.cnt[3]);
     out->n_dH_positive = int64_t(host.cnt[4]);
+    for (int b = 0; b < 4; ++b) out->n_xmax_band[b] = int64_t(host.cnt[5 + b]);
     if (alpha_hist)
         for (int b = 0; b < ELBM_HIST_BINS + 2; ++b) alpha_hist[b] = int64_t(host.hist[b]);
     if (out->n_nonpositive > 0)

@@ -131,7 +131,6 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
     const int G = gridDim.x;
     if (int(blockIdx.x) >= rows) return; // uniform over the CTA
     const uint32_t row_bytes = uint32_t(g.nx) * uint32_t(sizeof(S));
-    const T rho0 = rho0_of<T>(p);
     const int lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -209,13 +208,15 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
             for (int i = 0; i < Q; ++i) {
                 const int cx = vel(D, i, 0);
                 const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
-                f[i] = ST::load(tile[i * NXMAX + sx], T(weight(D, i)), rho0);
+                f[i] = ST::raw(tile[i * NXMAX + sx]);
             }
             int br;
-            collide<D, T, true>(f, xd, p, &br);
+            collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) {
+                const int cx = vel(D, i, 0);
+                return ST::raw(tile[i * NXMAX + (cx == 1 ? xm : (cx == -1 ? xp : x))]);
+            });
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                __stcs(fout + (int64_t)i * g.N + rowbase + x, ST::store(f[i], T(weight(D, i)), rho0));
+            for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + rowbase + x, ST::pack(f[i]));
         }
         // release the stage; the last warp out refills it
         __syncwarp();

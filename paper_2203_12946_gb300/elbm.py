@@ -29,7 +29,7 @@ ELBM_ERR_TIMEOUT = -5
 ELBM_D2Q9 = 9
 ELBM_D3Q27 = 27
 ELBM_BC_PERIODIC = 0
-ELBM_STORE_F64, ELBM_STORE_F32, ELBM_STORE_F16DEV, ELBM_STORE_BF16DEV = 0, 1, 2, 3
+ELBM_STORE_F64, ELBM_STORE_F32, ELBM_STORE_F16DEV, ELBM_STORE_BF16DEV, ELBM_STORE_F32DEV = 0, 1, 2, 3, 4
 ELBM_ALPHA_HIGHER, ELBM_ALPHA_LOWER, ELBM_ALPHA_LBGK, ELBM_ALPHA_ITERATE1 = 0, 1, 2, 3
 ELBM_B_DERIVED, ELBM_B_PRINTED = 0, 1
 ELBM_MEM_DEVICE, ELBM_MEM_HOST = 0, 1
@@ -40,8 +40,18 @@ ELBM_HIST_BINS = 256
 ELBM_NOALLOC_SCRATCH_BYTES = 4096
 
 STORAGE_NAMES = {"f64": ELBM_STORE_F64, "f32": ELBM_STORE_F32, "f16dev": ELBM_STORE_F16DEV,
-                 "bf16dev": ELBM_STORE_BF16DEV}
-STORAGE_BYTES = {ELBM_STORE_F64: 8, ELBM_STORE_F32: 4, ELBM_STORE_F16DEV: 2, ELBM_STORE_BF16DEV: 2}
+                 "bf16dev": ELBM_STORE_BF16DEV, "f32dev": ELBM_STORE_F32DEV}
+STORAGE_BYTES = {ELBM_STORE_F64: 8, ELBM_STORE_F32: 4, ELBM_STORE_F16DEV: 2, ELBM_STORE_BF16DEV: 2,
+                 ELBM_STORE_F32DEV: 4}
+# numpy type of one stored element (bfloat16 as its raw 16 bits)
+STORAGE_NUMPY = {ELBM_STORE_F64: np.float64, ELBM_STORE_F32: np.float32, ELBM_STORE_F16DEV: np.float16,
+                 ELBM_STORE_BF16DEV: np.uint16, ELBM_STORE_F32DEV: np.float32}
+
+
+def dev_unit(D: int, rho0: float = 1.0) -> float:
+    """R of the deviation storages (include/elbm.h): 6^-D rho0 rounded to FP32; population i
+    is stored as f_i - k_i R with w_i = k_i 6^-D."""
+    return float(np.float32((1.0 / 36.0 if D == 2 else 1.0 / 216.0) * rho0))
 
 EXPORTED = ["elbm_default_opts", "elbm_population_bytes", "elbm_create", "elbm_destroy",
             "elbm_last_error", "elbm_bind_buffers", "elbm_set_stream", "elbm_init_equilibrium",
@@ -68,11 +78,13 @@ class elbm_diag(ctypes.Structure):
                 ("alpha_max", ctypes.c_double), ("alpha_mean", ctypes.c_double),
                 ("n_nodes", ctypes.c_int64), ("n_cutoff", ctypes.c_int64),
                 ("n_solved", ctypes.c_int64), ("n_clamped", ctypes.c_int64),
-                ("n_nonpositive", ctypes.c_int64), ("n_dH_positive", ctypes.c_int64)]
+                ("n_nonpositive", ctypes.c_int64), ("n_dH_positive", ctypes.c_int64),
+                ("n_xmax_band", ctypes.c_int64 * 4)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["momentum"] = list(self.momentum)
+        d["n_xmax_band"] = list(self.n_xmax_band)
         return d
 
 
@@ -443,16 +455,14 @@ class Simulation:
 
     def get_populations(self):
         """Host copy of the stored populations as numpy, shape (Q, N), storage dtype
-        (bf16 is returned as raw uint16)."""
-        dt = {ELBM_STORE_F64: np.float64, ELBM_STORE_F32: np.float32,
-              ELBM_STORE_F16DEV: np.float16, ELBM_STORE_BF16DEV: np.uint16}[self.storage]
+        (bf16 is returned as raw uint16; deviation storages hold f_i - k_i R)."""
+        dt = STORAGE_NUMPY[self.storage]
         out = np.empty((self.Q, self.N), dtype=dt)
         elbm_get_populations(self.h, out, ELBM_MEM_HOST)
         return out
 
     def set_populations(self, f):
-        dt = {ELBM_STORE_F64: np.float64, ELBM_STORE_F32: np.float32,
-              ELBM_STORE_F16DEV: np.float16, ELBM_STORE_BF16DEV: np.uint16}[self.storage]
+        dt = STORAGE_NUMPY[self.storage]
         f = np.ascontiguousarray(f, dtype=dt).reshape(self.Q, self.N)
         elbm_set_populations(self.h, f, ELBM_MEM_HOST)
 
@@ -599,8 +609,7 @@ class Ensemble:
     """Independent periodic domains advanced together (see the batched-ensemble
     section of include/elbm.h)."""
 
-    _DT = {ELBM_STORE_F64: np.float64, ELBM_STORE_F32: np.float32, ELBM_STORE_F16DEV: np.float16,
-           ELBM_STORE_BF16DEV: np.uint16}
+    _DT = STORAGE_NUMPY
 
     def __init__(self, lattice, dims_list, betas, storage="f32", alpha_mode=ELBM_ALPHA_HIGHER, cutoff=True,
                  b_variant=ELBM_B_DERIVED, device=0, rho0=1.0, stream=None):

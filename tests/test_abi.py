@@ -183,3 +183,21 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(sname, "size")] == ctypes.sizeof(cls), sname
         for fname, _ in cls._fields_:
             assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
+
+
+def test_noalloc_rejects_wrapping_dims_and_misaligned_buffers_before_cuda(lib):
+    """elbm_diagnostics_noalloc decides its argument errors on the host before any CUDA
+    call (so they come back as ELBM_ERR_ARG here, without a GPU): sides of up to 2^30 whose
+    product wraps around in 64 bits (2^30 * 2^30 * 2^4 = 2^64 reads as 0, * 2^5 as 2) are
+    more than 2^31 nodes, and a buffer address that is not a multiple of the element size
+    is refused before it could be read."""
+    fn = lib.elbm_diagnostics_noalloc
+    d = E.elbm_diag()
+    opts = E.elbm_default_opts()
+    for dims in ((1 << 30, 1 << 30, 1 << 4), (1 << 30, 1 << 30, 1 << 5), (1 << 30, 1 << 2, 1 << 30)):
+        code = fn(E.ELBM_D3Q27, E._dims(dims), 0.9, ctypes.byref(opts), 4096, ctypes.byref(d), None)
+        assert code == E.ELBM_ERR_ARG and "2^31" in E.elbm_last_error(None)
+    for storage, addr in ((E.ELBM_STORE_F32, 4098), (E.ELBM_STORE_F64, 4100), (E.ELBM_STORE_F16DEV, 4097)):
+        opts.storage = storage
+        code = fn(E.ELBM_D2Q9, E._dims((8, 8, 1)), 0.9, ctypes.byref(opts), addr, ctypes.byref(d), None)
+        assert code == E.ELBM_ERR_ARG and "aligned" in E.elbm_last_error(None)

@@ -200,3 +200,22 @@ def test_batch_domain_errors():
         assert ei.value.code == E.ELBM_ERR_ARG
         with pytest.raises(E.ElbmError):
             E.elbm_batch_step(ens.b, 1, 7)
+
+
+@pytest.mark.parametrize("mode", [E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_PERSISTENT])
+def test_more_domains_than_one_launch_table(mode):
+    """A batch of 70 domains needs two batched launches per step (a launch's parameter
+    table holds 64 domains); uneven sides, each domain against the oracle (FP64)."""
+    rng = np.random.default_rng(70)
+    dims = [(int(a), int(b), 1) for a, b in zip(rng.integers(3, 40, size=70), rng.integers(2, 30, size=70))]
+    betas = list(rng.uniform(0.9, 0.999, size=70))
+    f0 = [domain_state(2, d, 3e-3, seed=200 + k) for k, d in enumerate(dims)]
+    with E.Ensemble(E.ELBM_D2Q9, dims, betas, storage="f64", cutoff=False) as ens:
+        for k in range(len(dims)):
+            ens.set_populations(k, f0[k])
+        ens.step(3, mode)
+        got = [ens.get_populations(k) for k in range(len(dims))]
+        ens.synchronize()
+    for k, d in enumerate(dims):
+        want, *_ = O.step(2, d, f0[k], betas[k], cutoff=False, nsteps=3)
+        assert np.max(np.abs(got[k] - want) / want) < 1e-12, k

@@ -50,11 +50,36 @@ def noisy_state(D, dims, eps, seed=3, u0=0.05, kind="tgv"):
     return f * inputs.population_noise(3 ** D, X.size, eps, seed=seed)
 
 
+def dev_ref(D):
+    """Reference c_i = k_i R of the deviation storages (rho0 = 1): w_i = k_i 6^-D, R = 6^-D
+    rounded to FP32 (include/elbm.h)."""
+    _, w = O.lattice(D)
+    return np.rint(w * 6.0 ** D) * E.dev_unit(D)
+
+
+def stored(D, f, storage):
+    """(values to hand to set_populations, the FP64 populations they represent exactly)
+    for an oracle field f and an FP32 storage."""
+    if storage == "f32dev":
+        c = dev_ref(D)[:, None]
+        s = (f - c).astype(np.float32)
+        return s, c + s.astype(np.float64)
+    s = f.astype(np.float32)
+    return s, s.astype(np.float64)
+
+
+def populations(D, raw, storage):
+    """FP64 populations of a stored field (get_populations output)."""
+    if storage == "f32dev":
+        return dev_ref(D)[:, None] + raw.astype(np.float64)
+    return raw.astype(np.float64)
+
+
 def gpu_run(D, dims, beta, f0, nsteps, storage="f64", **kw):
     with E.Simulation(LAT[D], dims, beta, storage=storage, **kw) as sim:
         sim.set_populations(f0)
         sim.step(nsteps)
-        f = sim.get_populations().astype(np.float64)
+        f = populations(D, sim.get_populations(), storage)
         sim.synchronize()  # also reports an expired device-side wait
     return f
 
@@ -148,19 +173,44 @@ def test_config1_taylor_green_64_fp64_1000_steps():
         assert np.max(np.abs(r_g - r_o)) < 1e-12
 
 
+def test_config1_alpha_field_fp64():
+    """The 64^2 Taylor-Green configuration (u0 = 0.01, beta = 0.9, cutoff off), every 100
+    steps up to 1000: the GPU's FP64 path length of the next collision (elbm_alpha_field) on
+    the oracle's state equals the oracle's alpha_H to 1e-12, and on the GPU's own state
+    (which differs from the oracle's by rounding order) to 1e-11."""
+    L, beta = 64, 0.9
+    dims = (L, L, 1)
+    X, Y, _ = inputs.grid(dims)
+    rho, u = inputs.taylor_green_2d(X, Y, L, u0=0.01)
+    f_o = O.init_equilibrium(2, rho, u)
+    with E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64", cutoff=False) as run, \
+            E.Simulation(E.ELBM_D2Q9, dims, beta, storage="f64", cutoff=False) as probe:
+        run.set_populations(f_o)
+        for t in range(100, 1001, 100):
+            f_o, *_ = O.step(2, dims, f_o, beta, cutoff=False, nsteps=100)
+            run.step(100)
+            a_o, br_o, _ = O.alpha_field(2, O.stream(2, dims, f_o), beta, cutoff=False)
+            probe.set_populations(f_o)
+            a_p, fl_p = [x.cpu().numpy() for x in probe.alpha_field()]
+            a_r, _ = [x.cpu().numpy() for x in run.alpha_field()]
+            assert np.array_equal(fl_p, br_o)
+            assert np.max(np.abs(a_p - a_o)) < 1e-12, t
+            assert np.max(np.abs(a_r - a_o)) < 1e-11, t
+
+
 # ---------------------------------------------------------------------------
 # FP32
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("D,dims", [(2, (300, 37, 1)), (3, (37, 19, 11))])
 @pytest.mark.parametrize("cutoff", [True, False])
-def test_fp32_single_step(D, dims, cutoff):
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+def test_fp32_single_step(D, dims, cutoff, storage):
     beta = 0.999
-    f0 = noisy_state(D, dims, 4e-3).astype(np.float32)
-    f_gpu = gpu_run(D, dims, beta, f0, 1, "f32", cutoff=cutoff)
-    f_in = f0.astype(np.float64)
+    f0, f_in = stored(D, noisy_state(D, dims, 4e-3), storage)
+    f_gpu = gpu_run(D, dims, beta, f0, 1, storage, cutoff=cutoff)
     f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=cutoff, want_alpha=True)
-    with E.Simulation(LAT[D], dims, beta, storage="f32", cutoff=cutoff) as sim:
+    with E.Simulation(LAT[D], dims, beta, storage=storage, cutoff=cutoff) as sim:
         sim.set_populations(f0)
         a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]
     agree = check_branches(D, O.stream(D, dims, f_in), fl, br_ora, 1e-6)
@@ -170,19 +220,19 @@ def test_fp32_single_step(D, dims, cutoff):
 
 
 @pytest.mark.parametrize("D,dims", [(2, (211, 53, 1)), (3, (31, 17, 13))])
-def test_fp32_series_and_exact_paths(D, dims):
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+def test_fp32_series_and_exact_paths(D, dims, storage):
     """Noise levels whose |x|max straddles 0.02, where the FP32 collision switches between
     power-series and per-population forms of its coefficients: both agree with the oracle
     at FP32 precision, and nodes on either side are present."""
     beta = 0.995
-    f0 = noisy_state(D, dims, 0.016 if D == 2 else 0.012, seed=43).astype(np.float32)
-    f_in = f0.astype(np.float64)
-    f_gpu = gpu_run(D, dims, beta, f0, 1, "f32", cutoff=True)
+    f0, f_in = stored(D, noisy_state(D, dims, 0.016 if D == 2 else 0.012, seed=43), storage)
+    f_gpu = gpu_run(D, dims, beta, f0, 1, storage, cutoff=True)
     f_pre = O.stream(D, dims, f_in)
     f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=True, want_alpha=True)
     xm = xabsmax_of(D, f_pre)
     assert np.sum(xm < 0.019) > 50 and np.sum(xm > 0.021) > 50
-    with E.Simulation(LAT[D], dims, beta, storage="f32", cutoff=True) as sim:
+    with E.Simulation(LAT[D], dims, beta, storage=storage, cutoff=True) as sim:
         sim.set_populations(f0)
         a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]
     agree = check_branches(D, f_pre, fl, br_ora, 1e-6)
@@ -192,16 +242,16 @@ def test_fp32_series_and_exact_paths(D, dims):
 
 
 @pytest.mark.parametrize("D,dims", [(2, (131, 29, 1)), (3, (21, 13, 9))])
-def test_fp32_iterate1_mode(D, dims):
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+def test_fp32_iterate1_mode(D, dims, storage):
     """alpha_Iterate1 (Sec. IV) in FP32 against the oracle, including nodes far enough
     from equilibrium that the Newton step is undefined and alpha_Lower is kept."""
     beta = 0.99
-    f0 = noisy_state(D, dims, 0.5, seed=8).astype(np.float32)
-    f_in = f0.astype(np.float64)
+    f0, f_in = stored(D, noisy_state(D, dims, 0.5, seed=8), storage)
     gm, om = MODES["iterate1"]
-    f_gpu = gpu_run(D, dims, beta, f0, 1, "f32", alpha_mode=gm, cutoff=True)
+    f_gpu = gpu_run(D, dims, beta, f0, 1, storage, alpha_mode=gm, cutoff=True)
     f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=True, mode=om, want_alpha=True)
-    with E.Simulation(LAT[D], dims, beta, storage="f32", alpha_mode=gm, cutoff=True) as sim:
+    with E.Simulation(LAT[D], dims, beta, storage=storage, alpha_mode=gm, cutoff=True) as sim:
         sim.set_populations(f0)
         a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]
     agree = check_branches(D, O.stream(D, dims, f_in), fl, br_ora, 1e-6)
@@ -235,7 +285,8 @@ def test_subgrid_viscosity(D, dims, storage, tol):
 
 
 @pytest.mark.parametrize("D,L,nsteps", [(2, 96, 40), (3, 32, 20)])
-def test_fp32_taylor_green_velocity(D, L, nsteps):
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+def test_fp32_taylor_green_velocity(D, L, nsteps, storage):
     """Taylor-Green vortex (u0 = 0.05, beta = 0.999) from the equilibrium, FP32 storage and
     arithmetic: u within 1e-5 relative (L2) of the FP64 oracle started from the same
     FP32-rounded populations, with the closed-form alpha active on most nodes."""
@@ -244,13 +295,13 @@ def test_fp32_taylor_green_velocity(D, L, nsteps):
     X, Y, Z = inputs.grid(dims)
     rho, u = (inputs.taylor_green_2d(X, Y, L, u0=0.05) if D == 2
               else inputs.taylor_green_3d(X, Y, Z, L, u0=0.05))
-    with E.Simulation(LAT[D], dims, beta, storage="f32") as sim:
+    with E.Simulation(LAT[D], dims, beta, storage=storage) as sim:
         sim.init_equilibrium(rho, u)
-        f_init = sim.get_populations().astype(np.float64)
+        f_init = populations(D, sim.get_populations(), storage)
         sim.step(nsteps)
         r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
         d = sim.diagnostics()
-    f_o0 = O.init_equilibrium(D, rho, u).astype(np.float32).astype(np.float64)
+    _, f_o0 = stored(D, O.init_equilibrium(D, rho, u), storage)
     assert np.array_equal(f_init, f_o0)
     f_o, *_ = O.step(D, dims, f_o0, beta, nsteps=nsteps)
     r_o, u_o = O.moments_field(D, f_o)
@@ -260,23 +311,46 @@ def test_fp32_taylor_green_velocity(D, L, nsteps):
 
 
 @pytest.mark.parametrize("D,dims,nsteps", [(2, (128, 77, 1), 20), (3, (29, 23, 17), 10)])
-def test_fp32_noisy_multistep(D, dims, nsteps):
-    """Strongly non-equilibrium start (0.3% noise on every population).  The FP32 rounding of
-    f^eq (a few ulp per population) breaks the collision's momentum balance by at most
-    ~D * 1e-7 rho per node and step, so |u_gpu - u_oracle| <= 2e-7 D nsteps."""
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+def test_fp32_noisy_multistep(D, dims, nsteps, storage):
+    """Strongly non-equilibrium start (0.3% noise on every population): u within 1e-5
+    relative (L2) of the FP64 oracle started from the same stored state, with the cutoff on
+    and off."""
     beta = 0.999
-    f0 = noisy_state(D, dims, 3e-3, seed=13).astype(np.float32)
+    f0, f_in = stored(D, noisy_state(D, dims, 3e-3, seed=13), storage)
     for cutoff in (False, True):
-        with E.Simulation(LAT[D], dims, beta, storage="f32", cutoff=cutoff) as sim:
+        with E.Simulation(LAT[D], dims, beta, storage=storage, cutoff=cutoff) as sim:
             sim.set_populations(f0)
             sim.step(nsteps)
             r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
-            f_g = sim.get_populations().astype(np.float64)
-        f_o, *_ = O.step(D, dims, f0.astype(np.float64), beta, cutoff=cutoff, nsteps=nsteps)
+            f_g = populations(D, sim.get_populations(), storage)
+        f_o, *_ = O.step(D, dims, f_in, beta, cutoff=cutoff, nsteps=nsteps)
         r_o, u_o = O.moments_field(D, f_o)
-        assert np.max(np.abs(u_g - u_o)) < 2e-7 * D * nsteps
+        assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) < 1e-5
         assert np.max(np.abs(r_g - r_o)) < 1e-5
         assert np.max(np.abs(f_g - f_o) / f_o) < nsteps * 2e-6
+
+
+def test_fp32dev_taylor_green_1000_steps():
+    """D3Q27 Taylor-Green vortex (u0 = 0.05, beta = 0.999, the benchmark flow's parameters)
+    on 64^3 for 1000 steps from the equilibrium in FP32 deviation storage: u within 1e-5
+    relative (L2) of the FP64 oracle started from the same stored state.  At this length
+    the FP32 storage of f_i rounds at the scale of w_i every step and drifts past 1e-5;
+    storing d_i = f_i - c_i and colliding on it rounds at the scale of d_i instead."""
+    L, beta, nsteps = 64, 0.999, 1000
+    dims = (L, L, L)
+    X, Y, Z = inputs.grid(dims)
+    rho, u = inputs.taylor_green_3d(X, Y, Z, L, u0=0.05)
+    with E.Simulation(E.ELBM_D3Q27, dims, beta, storage="f32dev") as sim:
+        sim.init_equilibrium(rho, u)
+        f_init = populations(3, sim.get_populations(), "f32dev")
+        sim.step(nsteps)
+        _, u_g = [t.cpu().numpy() for t in sim.moments()]
+        d = sim.diagnostics()
+    f_o, *_ = O.step(3, dims, f_init, beta, nsteps=nsteps)
+    _, u_o = O.moments_field(3, f_o)
+    assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) < 1e-5
+    assert d["n_solved"] > 0.5 * X.size and d["n_nonpositive"] == 0
 
 
 def test_fp32_full_size_sampled_nodes():
@@ -367,7 +441,7 @@ def test_deviation_storage_single_step(storage, mant_bits):
 # companions: init, moments, alpha field, diagnostics, edge cases
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f32dev"])
 def test_init_and_moments(storage):
     D, dims = 3, (19, 13, 7)
     rng = np.random.default_rng(23)
@@ -376,11 +450,16 @@ def test_init_and_moments(storage):
     u = 0.1 * rng.standard_normal((3, N))
     with E.Simulation(E.ELBM_D3Q27, dims, 0.9, storage=storage) as sim:
         sim.init_equilibrium(rho, u)
-        f = sim.get_populations().astype(np.float64)
+        f = populations(3, sim.get_populations(), storage)
         r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
     f_o = O.init_equilibrium(3, rho, u)
-    tol = 1e-15 if storage == "f64" else 6e-8
-    assert np.max(np.abs(f - f_o) / f_o) < tol
+    if storage == "f32dev":
+        # f^eq - c_i rounded once to FP32: half an ulp of the deviation
+        c = dev_ref(3)[:, None]
+        assert np.all(np.abs(f - f_o) <= 2.0 ** -24 * np.abs(f_o - c) + 1e-15)
+    else:
+        tol = 1e-15 if storage == "f64" else 6e-8
+        assert np.max(np.abs(f - f_o) / f_o) < tol
     r_o, u_o = O.moments_field(3, f)
     assert np.max(np.abs(r_g - r_o)) < 1e-14 and np.max(np.abs(u_g - u_o)) < 1e-14
 
@@ -415,6 +494,7 @@ def test_diagnostics_against_oracle():
 @pytest.mark.parametrize("D,dims,storage,kernel,force", [
     (2, (77, 41, 1), "f32", E.ELBM_KERNEL_DIRECT, False),
     (3, (23, 19, 11), "f32", E.ELBM_KERNEL_DIRECT, False),
+    (3, (23, 19, 11), "f32dev", E.ELBM_KERNEL_DIRECT, False),
     (3, (23, 19, 11), "f64", E.ELBM_KERNEL_DIRECT, False),
     (2, (64, 40, 1), "f32", E.ELBM_KERNEL_ROWS, False),   # diagnostics pass, then the step
     (2, (61, 33, 1), "f32", E.ELBM_KERNEL_DIRECT, True),  # body force: diagnostics pass first
@@ -424,8 +504,8 @@ def test_step_diag_equals_diagnostics_then_steps(D, dims, storage, kernel, force
     leaves the same state; called twice in a row."""
     beta = 0.993
     f0 = noisy_state(D, dims, 4e-3, seed=47)
-    if storage == "f32":
-        f0 = f0.astype(np.float32)
+    if storage != "f64":
+        f0 = stored(D, f0, storage)[0]
     F = np.array([1e-4, -2e-4, 5e-5])[:D] if force else None
     with E.Simulation(LAT[D], dims, beta, storage=storage, kernel=kernel) as a, \
             E.Simulation(LAT[D], dims, beta, storage=storage, kernel=kernel) as b:
@@ -436,8 +516,8 @@ def test_step_diag_equals_diagnostics_then_steps(D, dims, storage, kernel, force
             want = a.diagnostics(with_hist=True)
             a.step(n)
             got = b.step_diag(n, with_hist=True)
-            fa = a.get_populations().astype(np.float64)
-            fb = b.get_populations().astype(np.float64)
+            fa = populations(D, a.get_populations(), storage)
+            fb = populations(D, b.get_populations(), storage)
             assert np.max(np.abs(fa - fb) / np.abs(fa)) < (1e-14 if storage == "f64" else 1e-6)
             for k in ("n_nodes", "n_cutoff", "n_solved", "n_clamped", "n_nonpositive", "n_dH_positive"):
                 assert got[k] == want[k], k
@@ -492,16 +572,17 @@ def test_degenerate_domains(D, dims):
 
 
 @pytest.mark.parametrize("D,dims,storage", [(2, (3, 70001, 1), "f32"), (2, (2, 66000, 1), "f64"),
-                                            (3, (2, 2, 65537), "f32")])
+                                            (3, (2, 2, 65537), "f32"), (3, (2, 65537, 2), "f32dev")])
 def test_one_dimensional_launch(D, dims, storage):
     """ny or nz above the grid limit of a 3D launch: the kernel runs on a 1D grid with
     64-bit node indices; same results as the oracle."""
     beta = 0.99
     f0 = noisy_state(D, dims, 3e-3, seed=41)
-    if storage == "f32":
-        f0 = f0.astype(np.float32)
+    f_in = f0
+    if storage != "f64":
+        f0, f_in = stored(D, f0, storage)
     f_gpu = gpu_run(D, dims, beta, f0, 2, storage, cutoff=False)
-    f_ora, *_ = O.step(D, dims, f0.astype(np.float64), beta, cutoff=False, nsteps=2)
+    f_ora, *_ = O.step(D, dims, f_in, beta, cutoff=False, nsteps=2)
     tol = 1e-12 if storage == "f64" else 4e-6
     assert np.max(np.abs(f_gpu - f_ora) / f_ora) < tol
 
@@ -635,3 +716,25 @@ def test_error_paths_of_the_force_and_fused_diagnostics_calls():
         assert ei.value.code == E.ELBM_ERR_ARG  # g_t aliases g_next
         d = sim.step_diag(2)  # the handle still works
         assert d["n_nodes"] == sim.N and sim.steps == 2
+
+
+@pytest.mark.parametrize("D,dims", [(3, (32, 20, 12)), (3, (256, 6, 5)), (2, (1024, 24, 1)), (2, (300, 37, 1))])
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+def test_rows_kernel_against_oracle(D, dims, storage):
+    """The ROWS kernel (rows staged in shared memory by bulk asynchronous copies) against the
+    FP64 oracle directly: one step on every node with the closed form everywhere (cutoff
+    off), within the FP32 per-step bound of the DIRECT kernel; then 12 steps with the
+    cutoff on, u within 1e-5 relative (L2)."""
+    beta = 0.999
+    f0, f_in = stored(D, noisy_state(D, dims, 4e-3, seed=61), storage)
+    f1 = gpu_run(D, dims, beta, f0, 1, storage, cutoff=False, kernel=E.ELBM_KERNEL_ROWS)
+    f_o1, *_ = O.step(D, dims, f_in, beta, cutoff=False, nsteps=1)
+    assert np.max(np.abs(f1 - f_o1) / f_o1) < 2e-6
+    with E.Simulation(LAT[D], dims, beta, storage=storage, cutoff=True, kernel=E.ELBM_KERNEL_ROWS) as sim:
+        sim.set_populations(f0)
+        sim.step(12)
+        _, u_g = [t.cpu().numpy() for t in sim.moments()]
+        sim.synchronize()
+    f_o, *_ = O.step(D, dims, f_in, beta, cutoff=True, nsteps=12)
+    _, u_o = O.moments_field(D, f_o)
+    assert np.linalg.norm(u_g - u_o) / np.linalg.norm(u_o) < 1e-5

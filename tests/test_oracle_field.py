@@ -98,3 +98,40 @@ def test_step_threads_agree():
     a, *_ = O.step(3, dims, f, 0.99, nsteps=3, nthreads=1)
     b, *_ = O.step(3, dims, f, 0.99, nsteps=3, nthreads=4)
     assert np.array_equal(a, b)
+
+
+def test_config1_alpha_higher_vs_elbm_on_taylor_green():
+    """Closed-form against Newton-iterated path length (Sec. IV, Table I) on the states of
+    the 64^2 Taylor-Green configuration (u0 = 0.01, beta = 0.9): at steps 100, 200, ..., 1000
+    of the run (cutoff off), per node of the pre-collision field, alpha_H against
+    alpha_ELBM, the root of the mirror-state entropy equation.  The L1, L2 and L_inf norms of
+    alpha_H - alpha_ELBM stay below Table I's 64^2 row (the paper's cavity at Re 5000 is
+    further from equilibrium than this vortex), and each node's gap follows the leading
+    order (4/3)(beta^2 - 1) <f,x^3> / <f,x^2> of Sec. III (Eq. alphahigherlimit against the
+    mirror root's 2 + <f,x^3>/(3<f,x^2>)), to O(|x|^2)."""
+    import os
+
+    HERE = os.path.dirname(os.path.abspath(__file__))
+    table = np.loadtxt(os.path.join(HERE, "golden", "table1_alpha_higher_vs_elbm.txt"))
+    L1max, L2max, Linfmax = table[0, 1:]
+    L, beta = 64, 0.9
+    dims = (L, L, 1)
+    X, Y, _ = inputs.grid(dims)
+    rho, u = inputs.taylor_green_2d(X, Y, L, u0=0.01)
+    f = O.init_equilibrium(2, rho, u)
+    worst = 0.0
+    for t in range(100, 1001, 100):
+        f, *_ = O.step(2, dims, f, beta, cutoff=False, nsteps=100)
+        fs = O.stream(2, dims, f)  # what the next collision sees
+        aH, br, aE = O.alpha_field(2, fs, beta, cutoff=False, want_elbm=True)
+        assert np.all(br == O.BRANCH_SOLVED) and np.all(np.isfinite(aE))
+        d = np.abs(aH - aE)
+        assert d.mean() < L1max and np.sqrt(np.mean(d ** 2)) < L2max and d.max() < Linfmax, t
+        for n in range(0, X.size, 97):
+            r, un = O.moments(2, fs[:, n])
+            x = O.departure(fs[:, n], O.equilibrium(2, r, un))
+            gap = (4.0 / 3.0) * (beta ** 2 - 1) * np.sum(fs[:, n] * x ** 3) / np.sum(fs[:, n] * x ** 2)
+            err = abs((aH[n] - aE[n]) - gap)
+            assert err < 30 * np.max(np.abs(x)) ** 2, (t, n)
+            worst = max(worst, err / np.max(np.abs(x)) ** 2)
+    assert worst > 0.0
