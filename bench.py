@@ -185,7 +185,7 @@ class Replicas:
 
 def xmax_bands(d: dict, N: int) -> dict:
     """Shares of nodes by |x|max of the next collision (the diagnostics' bands)."""
-    names = ["cutoff_lt_1e-3", "short_series_lt_5e-3", "long_series_lt_2e-2", "per_population_ge_2e-2"]
+    names = ["cutoff_lt_1e-3", "short_series_lt_5e-3", "long_series_lt_4e-2", "per_population_ge_4e-2"]
     return {k: v / N for k, v in zip(names, d["n_xmax_band"])}
 
 

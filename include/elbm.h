@@ -152,7 +152,7 @@ typedef struct elbm_diag {
                               violation beyond the rounding of alpha)                   */
     int64_t n_xmax_band[4]; /* nodes by |x|max of the next collision (Eq. xdef) in
                                [0, 1e-3) (the cutoff of Appendix D), [1e-3, 5e-3),
-                               [5e-3, 2e-2) and [2e-2, inf) (where the FP32 path
+                               [5e-3, 4e-2) and [4e-2, inf) (where the FP32 path
                                takes its short series, long series and per-population
                                forms of the path-length coefficients)                   */
 } elbm_diag;

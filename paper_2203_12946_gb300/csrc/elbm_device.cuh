@@ -16,8 +16,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 namespace eelbm {
 
 // ---------------------------------------------------------------------------
@@ -155,14 +153,17 @@ __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 // Storage traits.  raw/pack convert between the stored element and the compute
 // type as they are (populations, or deviations d_i = f_i - c_i where kDev);
 // load/store (and load64/store64 for FP64 companions) take the reference c_i of
-// population i and convert to and from populations f_i.  The step kernels
-// collide on the raw values: for deviation storage the collision works on d_i
-// directly (collide_stored), so no rounding happens at the scale of w_i.
+// population i and convert to and from populations f_i.  The step kernels load
+// with step_in and store with step_out, which give the values the collision
+// works on: the deviations themselves where kDevCollide (FP32 deviations, so that
+// no rounding happens at the scale of w_i), populations otherwise (the 16-bit
+// storages, whose quantisation to 11 or 8 significant bits dwarfs the FP32
+// rounding of f).
 // ---------------------------------------------------------------------------
 struct StoreF64 {
     using S = double;
     using T = double;
-    static constexpr bool kDev = false;
+    static constexpr bool kDev = false, kDevCollide = false;
     static constexpr int kRows = 0; // row-staged kernel not instantiated (FP64 is the parity path)
     __device__ static __forceinline__ T raw(S s) { return s; }
     __device__ static __forceinline__ S pack(T v) { return v; }
@@ -174,7 +175,7 @@ struct StoreF64 {
 struct StoreF32 {
     using S = float;
     using T = float;
-    static constexpr bool kDev = false;
+    static constexpr bool kDev = false, kDevCollide = false;
     static constexpr int kRows = 1;
     __device__ static __forceinline__ T raw(S s) { return s; }
     __device__ static __forceinline__ S pack(T v) { return v; }
@@ -186,7 +187,7 @@ struct StoreF32 {
 struct StoreF32Dev {
     using S = float;
     using T = float;
-    static constexpr bool kDev = true;
+    static constexpr bool kDev = true, kDevCollide = true;
     static constexpr int kRows = 1;
     __device__ static __forceinline__ T raw(S s) { return s; }
     __device__ static __forceinline__ S pack(T v) { return v; }
@@ -198,7 +199,7 @@ struct StoreF32Dev {
 struct StoreF16Dev {
     using S = __half;
     using T = float;
-    static constexpr bool kDev = true;
+    static constexpr bool kDev = true, kDevCollide = false;
     static constexpr int kRows = 1;
     __device__ static __forceinline__ T raw(S s) { return __half2float(s); }
     __device__ static __forceinline__ S pack(T v) { return __float2half_rn(v); }
@@ -210,7 +211,7 @@ struct StoreF16Dev {
 struct StoreBF16Dev {
     using S = __nv_bfloat16;
     using T = float;
-    static constexpr bool kDev = true;
+    static constexpr bool kDev = true, kDevCollide = false;
     static constexpr int kRows = 1;
     __device__ static __forceinline__ T raw(S s) { return __bfloat162float(s); }
     __device__ static __forceinline__ S pack(T v) { return __float2bfloat16_rn(v); }
@@ -219,6 +220,21 @@ struct StoreBF16Dev {
     __device__ static __forceinline__ double load64(S s, double c) { return c + double(__bfloat162float(s)); }
     __device__ static __forceinline__ S store64(double f, double c) { return __double2bfloat16(f - c); }
 };
+
+// The values a step kernel collides on (see kDevCollide), from the stored element s of
+// population i with reference c, and back.
+template <class ST>
+__device__ __forceinline__ typename ST::T step_in(typename ST::S s, typename ST::T c)
+{
+    if constexpr (ST::kDevCollide || !ST::kDev) return ST::raw(s);
+    else return ST::load(s, c);
+}
+template <class ST>
+__device__ __forceinline__ typename ST::S step_out(typename ST::T v, typename ST::T c)
+{
+    if constexpr (ST::kDevCollide || !ST::kDev) return ST::pack(v);
+    else return ST::store(v, c);
+}
 
 template <class T>
 __device__ __forceinline__ T g_entropy(T y);
@@ -467,15 +483,11 @@ __device__ __forceinline__ T node_collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<
 // term of the other set is exactly zero, so the sums equal the restricted ones.
 // The populations are reached through an accessor pa (pa.get(k): pair k; pa.put(k, v):
 // the post-collision pair k); the kernels pass PairRegs, the pairs held in registers.
-// Deviation form (kDev): the pairs hold d_i until the departures are formed (every
-// difference there is taken at the scale of d_i), then f_i = k_i R + d_i, rounded, for
-// the sums (which need f only to FP32 relative accuracy); the relaxation
-// d*_i = d_i + alpha beta x_i f_i takes d_i again from reload(i), the stored value
-// (a second read of the same element, normally an L1 hit), so the deviation form keeps
-// the register footprint of the population form.
+// Deviation form (kDev): the pairs hold d_i throughout; the departures are formed at
+// the scale of d_i, the sums use f_i = k_i R + d_i (needed only to FP32 relative
+// accuracy) and the relaxation is d*_i = d_i + alpha beta x_i f_i.
 //   in : pa.get  pre-collision populations (deviations d_i = f_i - k_i R when kDev),
 //                pair layout
-//        reload  (kDev and kRelax) the stored value of population i
 //   out: pa.put  post-collision values of the same kind (when kRelax)
 //        xp[NP]  departures x_i (Eq. xdef), pair layout
 //        returns alpha; *branch receives kBranch*
@@ -542,45 +554,18 @@ struct PairRegs {
     __device__ __forceinline__ void put(int k, float2 v) { a[k] = v; }
 };
 
-// A second read of a stored element for reload(i): an explicit load the compiler may not
-// merge with the first read of the same address (it would otherwise keep all Q values of
-// the first read live in registers through the collision).
-__device__ __forceinline__ float load_again(const float *q)
+// The same value, opaque to the compiler: k_i R + d_i formed again after the departures
+// instead of being kept from there (which would hold both f and d in registers).
+__device__ __forceinline__ float2 opaque(float2 v)
 {
-    float v;
-    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(q));
+    asm volatile("" : "+f"(v.x), "+f"(v.y));
     return v;
 }
-__device__ __forceinline__ double load_again(const double *q)
-{
-    double v;
-    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(q));
-    return v;
-}
-__device__ __forceinline__ __half load_again(const __half *q)
-{
-    unsigned short v;
-    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(v) : "l"(q));
-    return __ushort_as_half(v);
-}
-__device__ __forceinline__ __nv_bfloat16 load_again(const __nv_bfloat16 *q)
-{
-    unsigned short v;
-    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(v) : "l"(q));
-    return __ushort_as_bfloat16(v);
-}
 
-// Stand-in for kernels that never relax deviation storage.
-struct NoReload {
-    __device__ __forceinline__ float operator()(int) const { return 0.0f; }
-};
-
-template <int D, bool kRelax = true, bool kDev = false, class PA, class RL = NoReload>
+template <int D, bool kRelax = true, bool kDev = false, class PA>
 __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D>::NP], const CollideParams &p,
-                                                    int *branch, const RL &reload = RL{})
+                                                    int *branch)
 {
-    static_assert(!(kDev && kRelax) || !std::is_same<RL, NoReload>::value,
-                  "the deviation form's relaxation needs the stored values again (reload)");
     constexpr int Q = Lattice<D>::Q;
     constexpr int NP = Pairs<D>::NP;
     constexpr bool kPad = (Q % 2) == 1;
@@ -641,6 +626,16 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
         dr = 0.0f;
     }
     const float irho = rcp_nr(rho);
+    // f of pair k: the populations themselves, or k_i R + d_i (the padding lane has k = 0
+    // and holds 1); fagain(k) forms it anew past the departures
+    auto fval = [&](int k) -> float2 {
+        if constexpr (kDev) return pfma(f2(kpair<D>(k, 0), kpair<D>(k, 1)), f2(R), pa.get(k));
+        else return pa.get(k);
+    };
+    auto fagain = [&](int k) -> float2 {
+        if constexpr (kDev) return pfma(f2(kpair<D>(k, 0), kpair<D>(k, 1)), f2(R), opaque(pa.get(k)));
+        else return pa.get(k);
+    };
 
     // Per axis eps(c) = Upsilon z^c - 1 (as in node_collide).
     float eps[D][3];
@@ -692,8 +687,7 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
             delta = pfma(kr, E, psub(kr, pa.get(k)));
         }
         if (kPad && k == NP - 1) delta.y = 0.0f; // padding lane: f = 1, x = 0
-        if constexpr (kDev) pa.put(k, pfma(K, f2(R), pa.get(k))); // f = k_i R + d_i (padding: 0 R + 1)
-        const float2 xi = pmul(delta, prcp(pa.get(k)));
+        const float2 xi = pmul(delta, prcp(fval(k)));
         xp[k] = xi;
         xabs = fmaxf(xabs, fmaxf(fabsf(xi.x), fabsf(xi.y))); // three-input max
         xmin = fminf(xmin, fminf(xi.x, xi.y));
@@ -710,8 +704,9 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
         //   (60 + 60x + 11x^2)/(60 + 90x + 36x^2 + 3x^3)
         //       = 1 - x/2 + x^2/3 - x^3/4 + x^4/5 - ...      (c; log(1+x)/x to x^5)
         //   2/(4+t) + 1/(4+2t) + 2/(4+3t) = 5/4 - 5t/8 + 3t^2/8 - t^3/4 + ...   (b, t = k x)
-        // with the Omega+ sums P_m = M_m - S_m.  Kept to M6: at |x| = 0.02 the dropped
-        // terms are ~1e-10 of c1 and c and ~4e-9 of b.  Where |x|max < kShortX the
+        // with the Omega+ sums P_m = M_m - S_m.  Kept to M6: below |x|max = 0.04 the
+        // dropped terms move c1 by ~2e-9, c by ~1e-8 and b by ~4e-8 of themselves, and
+        // the path length by less than 7e-8 (half an FP32 ulp of 2).  Where |x|max < kShortX the
         // series stop at x^4 (M2..M4, S3, S4): the dropped terms are bounded by
         // |x|max^3 = 1.25e-7 of M2 times their coefficients (1/8 in c1, 1/4 in c), and
         // alpha moves by at most ~3e-8 relative, below FP32 rounding.  The series forms
@@ -720,7 +715,7 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
         // solving here: a warp whose lanes straddle a threshold runs the longer form
         // on all of them instead of each form in turn (the forms agree below FP32
         // rounding, so which one a lane gets moves its path length by less than that).
-        constexpr float kSeriesX = 0.02f, kShortX = 0.005f;
+        constexpr float kSeriesX = 0.04f, kShortX = 0.005f;
         const int form = __reduce_max_sync(__activemask(), xabs < kShortX ? 0 : (xabs < kSeriesX ? 1 : 2));
         const bool series = form < 2;
         float sb1, sc1, sc, s3, s4, s5 = 0.0f, s6 = 0.0f, m3 = 0.0f, m4 = 0.0f, m5 = 0.0f, m6 = 0.0f;
@@ -729,7 +724,7 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const float2 xi = xp[k];
-                const float2 fx2 = pmul(pa.get(k), pmul(xi, xi)); // f x^2
+                const float2 fx2 = pmul(fagain(k), pmul(xi, xi)); // f x^2
                 const float2 q3 = pmul(fx2, xi);
                 M2 = padd(M2, fx2);
                 M3 = padd(M3, q3);
@@ -752,7 +747,7 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
             for (int k = 0; k < NP; ++k) {
                 const float2 xi = xp[k];
                 const float2 x2 = pmul(xi, xi);
-                const float2 fx2 = pmul(pa.get(k), x2); // f x^2
+                const float2 fx2 = pmul(fagain(k), x2); // f x^2
                 const float2 q3 = pmul(fx2, xi);
                 const float2 q5 = pmul(q3, x2);
                 M2 = padd(M2, fx2);
@@ -780,7 +775,7 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const float2 xi = xp[k];
-                const float2 fx2 = pmul(pmul(pa.get(k), xi), xi); // f x^2
+                const float2 fx2 = pmul(pmul(fagain(k), xi), xi); // f x^2
                 const float2 K = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
                 const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), K)));
                 b1 = padd(b1, fx2);
@@ -818,7 +813,7 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
                         const float2 nu = pfma(pfma(f2(19.0f), t, f2(80.0f)), t, f2(80.0f));
                         const float2 de = pfma(pfma(pfma(f2(6.0f), t, f2(44.0f)), t, f2(96.0f)), t, f2(64.0f));
                         // f x^3 on Omega+ (0 elsewhere) times the bracket
-                        bp = pfma(pmul(pmul(pa.get(k), pmul(pmul(xi, xi), xq)), nu), prcp(de), bp);
+                        bp = pfma(pmul(pmul(fagain(k), pmul(pmul(xi, xi), xq)), nu), prcp(de), bp);
                     }
                     bsum = bp.x + bp.y;
                 }
@@ -844,15 +839,7 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
         // d* = d + alpha beta x f, rounded at the scale of d)
         const float2 ab = f2(alpha * beta);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            if constexpr (kDev) {
-                const int i1 = pair_pop(D, k, 1);
-                const float2 d = f2(reload(pair_pop(D, k, 0)), i1 >= 0 ? reload(i1) : 1.0f);
-                pa.put(k, pfma(pmul(ab, xp[k]), pa.get(k), d));
-            } else {
-                pa.put(k, pfma(pmul(ab, xp[k]), pa.get(k), pa.get(k)));
-            }
-        }
+        for (int k = 0; k < NP; ++k) pa.put(k, pfma(pmul(ab, xp[k]), fagain(k), pa.get(k)));
     }
     *branch = br;
     return alpha;
@@ -864,9 +851,9 @@ __device__ __forceinline__ float node_collide_pairs(PA &pa, float2 (&xp)[Pairs<D
 // FP64 through node_collide.  f holds populations (or deviations when kDev) and
 // receives the post-collision values of the same kind.
 // ---------------------------------------------------------------------------
-template <int D, class T, bool kRelax = true, bool kDev = false, class RL = NoReload>
+template <int D, class T, bool kRelax = true, bool kDev = false>
 __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q], const CollideParams &p,
-                                     int *branch, const RL &reload = RL{})
+                                     int *branch)
 {
     constexpr int Q = Lattice<D>::Q;
     if constexpr (sizeof(T) == 4) {
@@ -892,7 +879,7 @@ __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q
             fp[k] = make_float2(f[pair_pop(D, k, 0)], i1 >= 0 ? f[i1] : 1.0f);
         }
         PairRegs<NP> pr{fp};
-        const float alpha = node_collide_pairs<D, kRelax, kDev>(pr, xp, p, branch, reload);
+        const float alpha = node_collide_pairs<D, kRelax, kDev>(pr, xp, p, branch);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int sl = pair_slot(D, i);
@@ -906,36 +893,22 @@ __device__ __forceinline__ T collide(T (&f)[Lattice<D>::Q], T (&x)[Lattice<D>::Q
     }
 }
 
-// The collision of a step kernel on the values it loaded with ST::raw: deviations
-// for deviation storage, populations otherwise; stores them back with ST::pack.
-// reload(i) returns the stored value of population i again (ST::raw of the same
-// element), which the deviation form's relaxation reads a second time.
-template <int D, class ST, bool kRelax = true, class RL = NoReload>
+// The collision of a step kernel on the values it loaded with step_in: deviations for
+// the FP32 deviation storage, populations otherwise; they are stored back with step_out.
+template <int D, class ST, bool kRelax = true>
 __device__ __forceinline__ typename ST::T collide_stored(typename ST::T (&v)[Lattice<D>::Q],
                                                          typename ST::T (&x)[Lattice<D>::Q],
-                                                         const CollideParams &p, int *branch,
-                                                         const RL &reload = RL{})
+                                                         const CollideParams &p, int *branch)
 {
-    return collide<D, typename ST::T, kRelax, ST::kDev>(v, x, p, branch, reload);
+    return collide<D, typename ST::T, kRelax, ST::kDevCollide>(v, x, p, branch);
 }
 
 // ---------------------------------------------------------------------------
 // Pull streaming (Eq. advection): population i at node (x, y, z) comes from
 // (x - c_ix, y - c_iy, z - c_iz) with periodic wrap.
 // ---------------------------------------------------------------------------
-// Element offset of population i pulled into node (x, y, z): i N + source node.
-template <int D>
-__device__ __forceinline__ int64_t pull_offset(const Geometry &g, int x, int y, int z, int i)
-{
-    const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
-    const int sx = cx == 1 ? (x == 0 ? g.nx - 1 : x - 1) : (cx == -1 ? (x == g.nx - 1 ? 0 : x + 1) : x);
-    const int sy = cy == 1 ? (y == 0 ? g.ny - 1 : y - 1) : (cy == -1 ? (y == g.ny - 1 ? 0 : y + 1) : y);
-    const int sz = cz == 1 ? (z == 0 ? g.nz - 1 : z - 1) : (cz == -1 ? (z == g.nz - 1 ? 0 : z + 1) : z);
-    return (int64_t)i * g.N + ((int64_t)sz * g.ny + sy) * g.nx + sx;
-}
-
-// f receives populations (ST::load); with kRaw, the stored values as they are (ST::raw).
-template <int D, class ST, bool kRaw = false>
+// f receives populations (ST::load); with kStep, the values a step kernel collides on (step_in).
+template <int D, class ST, bool kStep = false>
 __device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin, const Geometry &g,
                                           int x, int y, int z, float R,
                                           typename ST::T (&f)[Lattice<D>::Q])
@@ -954,7 +927,7 @@ __device__ __forceinline__ void pull_load(const typename ST::S *__restrict__ fin
         const int sz = cz == 1 ? zm : (cz == -1 ? zp : z);
         const int64_t src = ((int64_t)sz * g.ny + sy) * g.nx + sx;
         const typename ST::S sv = __ldg(fin + (int64_t)i * g.N + src);
-        f[i] = kRaw ? ST::raw(sv) : ST::load(sv, dev_ref<D, T>(i, R));
+        f[i] = kStep ? step_in<ST>(sv, dev_ref<D, T>(i, R)) : ST::load(sv, dev_ref<D, T>(i, R));
     }
 }
 

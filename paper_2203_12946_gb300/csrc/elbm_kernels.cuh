@@ -99,23 +99,22 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
             return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
         };
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = ST::raw(__ldg(fin + src(i)));
-        collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(load_again(fin + src(i))); });
-        if constexpr (kForce) add_force<D, T, ST::kDev>(f, p);
+        for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(__ldg(fin + src(i)), dev_ref<D, T>(i, p.dunit_f));
+        collide_stored<D, ST, true>(f, xd, p, &br);
+        if constexpr (kForce) add_force<D, T, ST::kDevCollide>(f, p);
         const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::pack(f[i]));
+        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f)));
     } else {
         const int64_t n = (int64_t)blockIdx.x * kStepBlock + threadIdx.x;
         if (n >= g.N) return;
         int x, y, z;
         node_coords(n, g, x, y, z);
         pull_load<D, ST, true>(fin, g, x, y, z, p.dunit_f, f);
-        collide_stored<D, ST, true>(f, xd, p, &br,
-                                    [&](int i) { return ST::raw(load_again(fin + pull_offset<D>(g, x, y, z, i))); });
-        if constexpr (kForce) add_force<D, T, ST::kDev>(f, p);
+        collide_stored<D, ST, true>(f, xd, p, &br);
+        if constexpr (kForce) add_force<D, T, ST::kDevCollide>(f, p);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, ST::pack(f[i]));
+        for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + n, step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f)));
     }
 }
 
@@ -335,7 +334,7 @@ struct DiagThread {
             p_dmax = fmax(p_dmax, dH);
             if (dH > T(1e-6) * s3 && s3 > T(0)) cnt[4] += 1;
             // |x|max band: the cutoff of Appendix D, then the FP32 coefficient forms
-            cnt[xa < T(1e-3) ? 5 : (xa < T(5e-3) ? 6 : (xa < T(2e-2) ? 7 : 8))] += 1;
+            cnt[xa < T(1e-3) ? 5 : (xa < T(5e-3) ? 6 : (xa < T(4e-2) ? 7 : 8))] += 1;
         }
         p_al += alpha_t - T(2);
         cnt[br == kBranchCutoff ? 0 : (br == kBranchSolved ? 1 : 2)] += 1;
@@ -439,7 +438,7 @@ __global__ void __launch_bounds__(kAuxBlock) k_diag(const typename ST::S *__rest
         T f[Q], xd[Q], fc[Q];
         pull_load<D, ST, true>(fin, g, x, y, z, p.dunit_f, f); // stored values, as the step collides them
 #pragma unroll
-        for (int i = 0; i < Q; ++i) fc[i] = ST::kDev ? f[i] + dev_ref<D, T>(i, p.dunit_f) : f[i]; // populations
+        for (int i = 0; i < Q; ++i) fc[i] = ST::kDevCollide ? f[i] + dev_ref<D, T>(i, p.dunit_f) : f[i]; // populations
         int br;
         const T alpha_t = collide_stored<D, ST, false>(f, xd, p, &br);
         dt.node(fc, xd, alpha_t, br, p, s_hist);
@@ -489,15 +488,15 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
         };
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = ST::raw(__ldg(fin + src(i)));
-            fc[i] = ST::kDev ? f[i] + dev_ref<D, T>(i, p.dunit_f) : f[i]; // populations
+            f[i] = step_in<ST>(__ldg(fin + src(i)), dev_ref<D, T>(i, p.dunit_f));
+            fc[i] = ST::kDevCollide ? f[i] + dev_ref<D, T>(i, p.dunit_f) : f[i]; // populations
         }
         int br;
-        const T alpha_t = collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(load_again(fin + src(i))); });
+        const T alpha_t = collide_stored<D, ST, true>(f, xd, p, &br);
         dt.node(fc, xd, alpha_t, br, p, s_hist);
         const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), ST::pack(f[i]));
+        for (int i = 0; i < Q; ++i) __stcs(fout + (uint32_t(i) * N + n), step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f)));
     }
     diag_finish<kStepBlock>(dt, acc, s_hist);
 }
@@ -506,9 +505,9 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
 // Batched ensemble: one launch advances up to kBatchTableDomains domains.  Block
 // b is one work item, nodes x0 .. x0 + BX - 1 of one x-row of one domain; the
 // block finds its domain in the launch's parameter table (a coarse index, then a
-// forward scan over the item counts) and its row by division, both uniform over the block,
-// so each thread then addresses its populations as k_step does (32-bit offsets
-// inside the domain).  Each domain has its own beta; everything else is the
+// forward scan over the item counts) and its row by division, both uniform over the
+// block, so each thread then addresses its populations as k_step does (32-bit
+// offsets inside the domain).  Each domain has its own beta; everything else is the
 // single-domain step.
 // --------------------------------------------------------------------------
 template <class ST, int BX>
@@ -543,12 +542,12 @@ __global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restr
         return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
     };
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = ST::raw(__ldg(in + src(i)));
+    for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(__ldg(in + src(i)), dev_ref<D, T>(i, p.dunit_f));
     int br;
-    collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(load_again(in + src(i))); });
+    collide_stored<D, ST, true>(f, xd, p, &br);
     const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) __stcs(out + (uint32_t(i) * N + n), ST::pack(f[i]));
+    for (int i = 0; i < Q; ++i) __stcs(out + (uint32_t(i) * N + n), step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f)));
 }
 
 // --------------------------------------------------------------------------
@@ -626,12 +625,12 @@ __global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typen
                     return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
                 };
 #pragma unroll
-                for (int i = 0; i < Q; ++i) f[i] = ST::raw(in[src(i)]);
+                for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(in[src(i)], dev_ref<D, T>(i, p.dunit_f));
                 int br;
-                collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) { return ST::raw(in[src(i)]); });
+                collide_stored<D, ST, true>(f, xd, p, &br);
                 const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) out[uint32_t(i) * N + n] = ST::pack(f[i]);
+                for (int i = 0; i < Q; ++i) out[uint32_t(i) * N + n] = step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f));
             }
             __syncthreads(); // every store of this segment issued
             if (threadIdx.x == 0) {

@@ -65,7 +65,7 @@ constexpr int kDiagCounts = 9;
 struct DiagAcc {
     double sum[6]; // mass, momentum x/y/z, H, sum of alpha
     // cutoff, solved, clamped, nonpositive, dH-positive, then |x|max in
-    // [0, 1e-3), [1e-3, 5e-3), [5e-3, 2e-2), [2e-2, inf)
+    // [0, 1e-3), [1e-3, 5e-3), [5e-3, 4e-2), [4e-2, inf)
     unsigned long long cnt[kDiagCounts];
     unsigned long long dH_max_ord; // order-preserving encodings of doubles
     unsigned long long amin_ord;

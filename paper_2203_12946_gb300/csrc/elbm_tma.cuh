@@ -208,15 +208,12 @@ __global__ void __launch_bounds__(NT) k_step_rows(const typename ST::S *__restri
             for (int i = 0; i < Q; ++i) {
                 const int cx = vel(D, i, 0);
                 const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
-                f[i] = ST::raw(tile[i * NXMAX + sx]);
+                f[i] = step_in<ST>(tile[i * NXMAX + sx], dev_ref<D, T>(i, p.dunit_f));
             }
             int br;
-            collide_stored<D, ST, true>(f, xd, p, &br, [&](int i) {
-                const int cx = vel(D, i, 0);
-                return ST::raw(tile[i * NXMAX + (cx == 1 ? xm : (cx == -1 ? xp : x))]);
-            });
+            collide_stored<D, ST, true>(f, xd, p, &br);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + rowbase + x, ST::pack(f[i]));
+            for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + rowbase + x, step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f)));
         }
         // release the stage; the last warp out refills it
         __syncwarp();

@@ -222,16 +222,16 @@ def test_fp32_single_step(D, dims, cutoff, storage):
 @pytest.mark.parametrize("D,dims", [(2, (211, 53, 1)), (3, (31, 17, 13))])
 @pytest.mark.parametrize("storage", ["f32", "f32dev"])
 def test_fp32_series_and_exact_paths(D, dims, storage):
-    """Noise levels whose |x|max straddles 0.02, where the FP32 collision switches between
+    """Noise levels whose |x|max straddles 0.04, where the FP32 collision switches between
     power-series and per-population forms of its coefficients: both agree with the oracle
     at FP32 precision, and nodes on either side are present."""
     beta = 0.995
-    f0, f_in = stored(D, noisy_state(D, dims, 0.016 if D == 2 else 0.012, seed=43), storage)
+    f0, f_in = stored(D, noisy_state(D, dims, 0.032 if D == 2 else 0.024, seed=43), storage)
     f_gpu = gpu_run(D, dims, beta, f0, 1, storage, cutoff=True)
     f_pre = O.stream(D, dims, f_in)
     f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=True, want_alpha=True)
     xm = xabsmax_of(D, f_pre)
-    assert np.sum(xm < 0.019) > 50 and np.sum(xm > 0.021) > 50
+    assert np.sum(xm < 0.038) > 50 and np.sum(xm > 0.042) > 50
     with E.Simulation(LAT[D], dims, beta, storage=storage, cutoff=True) as sim:
         sim.set_populations(f0)
         a_gpu, fl = [t.cpu().numpy() for t in sim.alpha_field()]

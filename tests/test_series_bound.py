@@ -1,5 +1,5 @@
 """The FP32 collision sums the rational terms of the path-length coefficients from power
-series when |x|max < 0.02 (c1 from 2/(2+x), c from the Gauss-Legendre ratio, the Omega+
+series when |x|max < 0.04 (c1 from 2/(2+x), c from the Gauss-Legendre ratio, the Omega+
 Boole bracket of b in t = k x), truncated after x^6, and after x^4 when |x|max < 0.005.
 This checks, on the CPU, that the truncated forms reproduce the oracle's exact
 coefficients and path lengths below FP32 rounding on near-equilibrium states of both
@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 
-THRESHOLD = 0.02
+THRESHOLD = 0.04
 SHORT_THRESHOLD = 0.005
 
 
@@ -37,7 +37,9 @@ def truncated(f, x, beta, b_variant, top=6):
 @pytest.mark.parametrize("D", [2, 3])
 @pytest.mark.parametrize("b_variant", [O.B_DERIVED, O.B_PRINTED])
 @pytest.mark.parametrize("threshold,top,bounds", [
-    (THRESHOLD, 6, dict(c1=1e-9, c=1e-9, b=1e-8, alpha_lower=1e-9, alpha_higher=1e-8)),
+    # the dropped x^7.. terms at |x|max < 0.04: the path length moves by < 4e-8 of 2, half
+    # an FP32 ulp
+    (THRESHOLD, 6, dict(c1=4e-9, c=2e-8, b=6e-8, alpha_lower=4e-9, alpha_higher=5e-8)),
     # x^5 and x^6 dropped: |M5| <= |x|max^3 M2 = 1.25e-7 M2, so c1 and c move by at most
     # 1.6e-8 and 3.2e-8 of themselves, b by at most (2/15) 2 (0.375 (2x)^2 + ...) 2 x^3
     # ~ 0.8 |x|max^3 = 1e-7 of b1, and the path lengths stay below FP32 rounding
