@@ -607,12 +607,22 @@ __global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typen
             const uint32_t xb = uint32_t(dm.xblocks);
             const S *in = fin + dm.off;
             S *out = fout + dm.off;
-            // the segment's work items, numbered inside the domain: row-major (z, y), x-chunk
+            // the segment's work items, numbered inside the domain: row-major (z, y), then the
+            // x-chunk c; one division for the first item, then counters
+            uint32_t row = uint32_t(seg.y) / xb, c = uint32_t(seg.y) - row * xb;
+            uint32_t z = row / ny, y = row - z * ny;
             for (uint32_t w = uint32_t(seg.y); w < uint32_t(seg.z); ++w) {
-                const uint32_t row = w / xb;
-                const uint32_t x = (w - row * xb) * BX + threadIdx.x;
+                const uint32_t x = c * BX + threadIdx.x;
+                const uint32_t yc = y, zc = z;
+                if (++c == xb) { // next row
+                    c = 0;
+                    if (++y == ny) {
+                        y = 0;
+                        ++z;
+                    }
+                }
                 if (x >= nx) continue;
-                const uint32_t z = row / ny, y = row - z * ny;
+                const uint32_t y = yc, z = zc;
                 const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
                 const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
                 const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;

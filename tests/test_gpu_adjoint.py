@@ -3,7 +3,9 @@ differences of the forward step.
 
 * one backward step (elbm_adjoint_step) against the oracle's reverse step, whose node
   Jacobian-transpose products come from central differences of its own collision:
-  FP64 to the differences' accuracy (~1e-8), FP32 to 2e-4;
+  FP64 to the differences' accuracy (~1e-8), FP32 to 6e-7 (twice the largest relative
+  error measured on these states, 2.8e-7, which is the FP32 rounding of the VJP: the
+  FP64 path on the same FP32-rounded inputs agrees with the oracle to 4e-9);
 * whole rollouts: <dL/du0, v> from the autograd wrapper (with sqrt(T) checkpointing)
   against central differences of L along v computed with the FP64 forward, and the
   checkpointed gradient against the unsegmented one;
@@ -58,7 +60,7 @@ def test_adjoint_step_matches_oracle(D, dims, mode, storage):
         gt = torch.from_numpy(g.astype(np.float64 if storage == "f64" else np.float32)).cuda()
         got = sim.adjoint_step(ft, gt).double().cpu().numpy()
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
-    assert err < (1e-7 if storage == "f64" else 2e-4), err
+    assert err < (1e-7 if storage == "f64" else 6e-7), err
 
 
 def test_adjoint_through_clamp_matches_oracle():
