@@ -904,6 +904,304 @@ __device__ __forceinline__ typename ST::T collide_stored(typename ST::T (&v)[Lat
 }
 
 // ---------------------------------------------------------------------------
+// D2Q9 collision of two nodes at once, FP32.
+//
+// The arithmetic of node_collide_pairs, with the two lanes of every float2 holding
+// two different nodes (A in .x, B in .y) and population i in slot i.  All per-node
+// work -- moments, axis factors, the three quadratic roots of Eq. alphaLowerSoln and
+// Eq. qaud_tight, the clamp of Appendix D -- is one paired instruction for both nodes,
+// where the population-pair form spends one per node: a D2Q9 node has only nine
+// populations, so that scalar work is a large share of its collision.  The lanes never
+// mix; a node's result depends on its partner only through the coefficient form, chosen
+// once per warp over every lane that solves (as in node_collide_pairs; the forms agree
+// below FP32 rounding).  Where one node takes the cutoff (or has b1 <= 0) and the other
+// solves, both lanes are evaluated and the first keeps alpha = 2.
+//   in : f[9]  pre-collision values of both nodes (deviations d_i = f_i - k_i R when kDev)
+//   out: f[9]  post-collision values of the same kind (when kRelax)
+//        x[9]  departures x_i (Eq. xdef)
+//        returns alpha of both nodes; br[0], br[1] receive kBranch*
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 psqrt(float2 a) { return f2(sqrt_(a.x), sqrt_(a.y)); }
+__device__ __forceinline__ float2 pneg(float2 a) { return pmul(a, f2(-1.0f)); }
+// quad_root on both lanes
+__device__ __forceinline__ float2 pquad_root(float2 a, float2 b, float2 c)
+{
+    const float2 rb = prcp(b);
+    const float2 q = pmul(c, rb), pq = pmul(a, rb);
+    const float2 disc = pfma(pmul(f2(-4.0f), pq), q, f2(1.0f));
+    return pmul(padd(q, q), prcp(padd(f2(1.0f), psqrt(disc))));
+}
+
+template <bool kRelax = true, bool kDev = false>
+__device__ __forceinline__ float2 node_collide_x2(float2 (&f)[9], float2 (&x)[9], const CollideParams &p,
+                                                  int (&br)[2])
+{
+    constexpr int D = 2, Q = 9;
+    const float beta = p.beta_f;
+    const float R = p.dunit_f; // deviation form: f_i = k_i R + d_i
+    auto K = [](int i) { return f2(float(weight_k(D, i))); };
+    auto fval = [&](int i) -> float2 {
+        if constexpr (kDev) return pfma(K(i), f2(R), f[i]);
+        else return f[i];
+    };
+    auto fagain = [&](int i) -> float2 {
+        if constexpr (kDev) return pfma(K(i), f2(R), opaque(f[i]));
+        else return f[i];
+    };
+
+    // Moments (Sec. I) from d_i, along y first: per column (c_x fixed) s0 = sum of d,
+    // s1 = (c_y = +1) - (c_y = -1).
+    float2 s0[3], s1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float2 d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            d[c] = kDev ? f[3 * k + c] : psub(f[3 * k + c], f2(float(weight_k(D, 3 * k + c)) * float(weight_unit(D))));
+        s0[k] = padd(padd(d[0], d[2]), d[1]);
+        s1[k] = psub(d[2], d[0]);
+    }
+    float2 drho = padd(padd(s0[0], s0[1]), s0[2]);
+    const float2 j[2] = {psub(s0[2], s0[0]), padd(padd(s1[0], s1[1]), s1[2])};
+    float2 rho, r, dr;
+    if constexpr (kDev) {
+        // rho = 36 R + drho; r - R = W drho exactly (36 W = 1), kept apart as dr
+        rho = pfma(f2(36.0f), f2(R), drho);
+        dr = pfma(drho, f2(float(weight_unit(D))), pmul(drho, f2(weight_unit_lo<D, float>())));
+        r = f2(R);
+    } else {
+        drho = psub(drho, f2(float(36.0 * double(weight_unit_lo<D, float>()))));
+        rho = padd(f2(1.0f), drho);
+        r = pfma(rho, f2(float(weight_unit(D))), pmul(rho, f2(weight_unit_lo<D, float>())));
+        dr = f2(0.0f);
+    }
+    // 1/rho: approximate reciprocal and one Newton-Raphson step (as rcp_nr)
+    const float2 r0 = prcp(rho);
+    const float2 irho = pfma(r0, pfma(pneg(rho), r0, f2(1.0f)), r0);
+
+    // Per axis eps(c) = Upsilon z^c - 1 = (2t - 3u, -t, 2t + 3u), t = 3u^2/(1 + s).
+    float2 eps[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float2 u = pmul(j[a], irho);
+        const float2 uu3 = pmul(f2(3.0f), pmul(u, u));
+        const float2 t = pmul(uu3, prcp(padd(f2(1.0f), psqrt(padd(f2(1.0f), uu3)))));
+        const float2 t2 = padd(t, t), u3 = pmul(f2(3.0f), u);
+        eps[a][0] = psub(t2, u3);
+        eps[a][1] = pneg(t);
+        eps[a][2] = padd(t2, u3);
+    }
+
+    // x_i = (f^eq_i - f_i) / f_i with E_i = (1 + eps_x)(1 + eps_y) - 1, as in node_collide_pairs.
+    float xabs[2] = {0.0f, 0.0f}, xmin[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float2 A = eps[0][vel(D, i, 0) + 1], el = eps[1][vel(D, i, 1) + 1];
+        const float2 E = pfma(A, el, padd(A, el));
+        float2 delta;
+        if constexpr (kDev) {
+            const float2 t = pfma(f2(R), E, pfma(dr, E, dr));
+            delta = pfma(K(i), t, pneg(f[i]));
+        } else {
+            const float2 kr = pmul(K(i), r);
+            delta = pfma(kr, E, psub(kr, f[i]));
+        }
+        const float2 xi = pmul(delta, prcp(fval(i)));
+        x[i] = xi;
+        xabs[0] = fmaxf(xabs[0], fabsf(xi.x));
+        xabs[1] = fmaxf(xabs[1], fabsf(xi.y));
+        xmin[0] = fminf(xmin[0], xi.x);
+        xmin[1] = fminf(xmin[1], xi.y);
+    }
+
+    float2 alpha = f2(2.0f);
+    br[0] = br[1] = kBranchCutoff;
+    const bool lbgk = p.mode == kModeLBGK;
+    const bool need[2] = {!lbgk && !(p.cutoff && xabs[0] < float(kCutoff)),
+                          !lbgk && !(p.cutoff && xabs[1] < float(kCutoff))};
+    if (need[0] || need[1]) {
+        // Coefficient forms of node_collide_pairs: x^4 series below kShortX, x^6 series
+        // below kSeriesX, per-population rational terms above; one form per warp.
+        constexpr float kSeriesX = 0.04f, kShortX = 0.005f;
+        auto form_of = [&](int l) { return !need[l] ? 0 : (xabs[l] < kShortX ? 0 : (xabs[l] < kSeriesX ? 1 : 2)); };
+        const int form = __reduce_max_sync(__activemask(), max(form_of(0), form_of(1)));
+        const bool series = form < 2;
+        float2 sb1, sc1, sc, s3, s4, s5 = f2(0.0f), s6 = f2(0.0f), m3 = f2(0.0f), m4 = f2(0.0f), m5 = f2(0.0f),
+                                     m6 = f2(0.0f);
+        if (form == 0) {
+            float2 M2 = f2(0.0f), S3 = f2(0.0f), S4 = f2(0.0f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float2 xi = x[i];
+                const float2 fx2 = pmul(fagain(i), pmul(xi, xi));
+                const float2 q3 = pmul(fx2, xi);
+                M2 = padd(M2, fx2);
+                m3 = padd(m3, q3);
+                m4 = pfma(q3, xi, m4);
+                const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+                const float2 q = pmul(fx2, xm);
+                S3 = padd(S3, q);
+                S4 = pfma(q, xm, S4);
+            }
+            sb1 = pmul(f2(0.5f), M2);
+            sc1 = padd(M2, pfma(m3, f2(-0.5f), pmul(m4, f2(0.25f))));
+            sc = padd(M2, pfma(m3, f2(-0.5f), pmul(m4, f2(1.0f / 3.0f))));
+            s3 = S3, s4 = S4;
+        } else if (series) {
+            float2 M2 = f2(0.0f), S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f), S6 = f2(0.0f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float2 xi = x[i];
+                const float2 x2 = pmul(xi, xi);
+                const float2 fx2 = pmul(fagain(i), x2);
+                const float2 q3 = pmul(fx2, xi);
+                const float2 q5 = pmul(q3, x2);
+                M2 = padd(M2, fx2);
+                m3 = padd(m3, q3);
+                m4 = pfma(q3, xi, m4);
+                m5 = padd(m5, q5);
+                m6 = pfma(q5, xi, m6);
+                const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+                const float2 q = pmul(fx2, xm);
+                const float2 xm2 = pmul(xm, xm);
+                S3 = padd(S3, q);
+                S4 = pfma(q, xm, S4);
+                S5 = pfma(q, xm2, S5);
+                S6 = pfma(pmul(q, xm), xm2, S6);
+            }
+            sb1 = pmul(f2(0.5f), M2);
+            // <f, 2x^2/(2+x)> and c, Horner in the power sums
+            sc1 = padd(M2, pfma(m3, f2(-0.5f), pfma(m4, f2(0.25f), pfma(m5, f2(-0.125f), pmul(m6, f2(0.0625f))))));
+            sc = padd(M2, pfma(m3, f2(-0.5f), pfma(m4, f2(1.0f / 3.0f), pfma(m5, f2(-0.25f), pmul(m6, f2(0.2f))))));
+            s3 = S3, s4 = S4, s5 = S5, s6 = S6;
+        } else {
+            float2 b1 = f2(0.0f), c1 = f2(0.0f), c = f2(0.0f), S3 = f2(0.0f), S4 = f2(0.0f), S5 = f2(0.0f),
+                   S6 = f2(0.0f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float2 xi = x[i];
+                const float2 fx2 = pmul(pmul(fagain(i), xi), xi);
+                const float2 Kq = pfma(pfma(f2(3.0f), xi, f2(30.0f)), xi, f2(30.0f));
+                const float2 A = pmul(fx2, prcp(pmul(padd(f2(2.0f), xi), Kq)));
+                b1 = padd(b1, fx2);
+                c1 = pfma(A, Kq, c1);
+                c = pfma(pmul(A, xi), xi, c);
+                const float2 xm = f2(fminf(xi.x, 0.0f), fminf(xi.y, 0.0f));
+                const float2 q = pmul(fx2, xm);
+                const float2 xm2 = pmul(xm, xm);
+                S3 = padd(S3, q);
+                S4 = pfma(q, xm, S4);
+                S5 = pfma(q, xm2, S5);
+                S6 = pfma(pmul(q, xm), xm2, S6);
+            }
+            sb1 = pmul(f2(0.5f), b1);
+            sc1 = padd(c1, c1);
+            sc = pfma(f2(5.0f), c, sc1);
+            s3 = S3, s4 = S4, s5 = S5, s6 = S6;
+        }
+        const bool ok[2] = {need[0] && sb1.x > 0.0f, need[1] && sb1.y > 0.0f};
+        if (ok[0] || ok[1]) {
+            const float2 aL = pquad_root(pmul(f2(0.5f), s3), sb1, sc1); // alpha_Lower
+            float2 asol;
+            if (p.mode == kModeLower) {
+                asol = aL;
+            } else {
+                const float2 kk = p.b_variant ? aL : pmul(aL, f2(beta));
+                float2 bsum;
+                if (series) {
+                    const float2 p3 = psub(m3, s3), p4 = psub(m4, s4), p5 = psub(m5, s5), p6 = psub(m6, s6);
+                    bsum = pfma(f2(1.25f), p3,
+                                pmul(kk, pfma(f2(-0.625f), p4,
+                                              pmul(kk, pfma(f2(0.375f), p5, pmul(kk, pmul(f2(-0.25f), p6)))))));
+                } else {
+                    bsum = f2(0.0f);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const float2 xi = x[i];
+                        const float2 xq = f2(fmaxf(xi.x, 0.0f), fmaxf(xi.y, 0.0f));
+                        const float2 t = pmul(kk, xq);
+                        const float2 nu = pfma(pfma(f2(19.0f), t, f2(80.0f)), t, f2(80.0f));
+                        const float2 de = pfma(pfma(pfma(f2(6.0f), t, f2(44.0f)), t, f2(96.0f)), t, f2(64.0f));
+                        bsum = pfma(pmul(pmul(fagain(i), pmul(pmul(xi, xi), xq)), nu), prcp(de), bsum);
+                    }
+                }
+                const float bb = beta * beta;
+                const float2 b = pfma(pmul(f2(-(2.0f / 15.0f) * bb), aL), bsum, sb1);
+                const float2 h = pquad_root(pmul(f2(bb * (1.0f / 6.0f)), s3), b, sc);
+                const float2 hb = pmul(h, f2(beta));
+                // a = beta^2 (S3/6 - hb S4/12 + hb^2 S5/20 - hb^3 S6/5), Horner in hb
+                const float2 a = pmul(f2(bb), pfma(hb, pfma(hb, pfma(hb, pmul(f2(-0.2f), s6), pmul(f2(0.05f), s5)),
+                                                            pmul(f2(-1.0f / 12.0f), s4)),
+                                                   pmul(f2(1.0f / 6.0f), s3)));
+                asol = pquad_root(a, b, sc); // alpha_Higher
+            }
+            alpha = f2(ok[0] ? asol.x : 2.0f, ok[1] ? asol.y : 2.0f);
+            if (ok[0]) br[0] = kBranchSolved;
+            if (ok[1]) br[1] = kBranchSolved;
+        }
+    }
+    if (!lbgk) {
+        // positivity (Appendix D), per node: alpha beta (-x_min) > 1
+        const float2 lim = pmul(pmul(alpha, f2(beta)), f2(xmin[0], xmin[1]));
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            if ((l ? lim.y : lim.x) < -1.0f) {
+                const float amax = div_(-1.0f, beta * xmin[l]);
+                float al = 0.5f * (1.0f + amax);
+                if (al > amax) al = 0.5f * amax;
+                if (l) alpha.y = al;
+                else alpha.x = al;
+                br[l] = kBranchClamped;
+            }
+        }
+    }
+    if (kRelax) {
+        const float2 ab = pmul(alpha, f2(beta));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = pfma(pmul(ab, x[i]), fagain(i), f[i]);
+    }
+    return alpha;
+}
+
+// Nodes per thread of the step kernels: two for D2Q9 with FP32 arithmetic (the
+// two-node collision), one otherwise.
+template <int D, class ST>
+__host__ __device__ constexpr int nodes_per_thread()
+{
+    return (D == 2 && sizeof(typename ST::T) == 4) ? 2 : 1;
+}
+
+// Two nodes' collision in a step kernel, on the values loaded with step_in (as
+// collide_stored): node_collide_x2 where nodes_per_thread is 2 (alpha_Iterate1, a
+// comparison variant with logarithms, stays on the one-node path), else node by node.
+template <int D, class ST, bool kRelax = true>
+__device__ __forceinline__ void collide2_stored(typename ST::T (&fa)[Lattice<D>::Q],
+                                                typename ST::T (&fb)[Lattice<D>::Q], const CollideParams &p)
+{
+    using T = typename ST::T;
+    constexpr int Q = Lattice<D>::Q;
+    if constexpr (nodes_per_thread<D, ST>() == 2) {
+        if (p.mode != kModeIterate1) {
+            float2 v[9], x[9];
+            int br[2];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) v[i] = make_float2(fa[i], fb[i]);
+            node_collide_x2<kRelax, ST::kDevCollide>(v, x, p, br);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                fa[i] = v[i].x;
+                fb[i] = v[i].y;
+            }
+            return;
+        }
+    }
+    T x[Q];
+    int br;
+    collide_stored<D, ST, kRelax>(fa, x, p, &br);
+    collide_stored<D, ST, kRelax>(fb, x, p, &br);
+}
+
+// ---------------------------------------------------------------------------
 // Pull streaming (Eq. advection): population i at node (x, y, z) comes from
 // (x - c_ix, y - c_iy, z - c_iz) with periodic wrap.
 // ---------------------------------------------------------------------------

@@ -56,20 +56,43 @@ __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x
 // outweigh the spills, which fall in the per-population form of the coefficients
 // (large |x| only): 0.640 -> 0.627 ms per 256^3 step on GB300.  The 16-bit storages
 // lose with that cap (their loads and stores need more live values): 5 blocks, the
-// allocation they had unbounded.  D2Q9 with FP32 arithmetic: 4 blocks of 256 (at most
-// 64 registers).  FP64 (the parity path): no bound.  ELBM_STEP_MIN_BLOCKS overrides.
+// allocation they had unbounded.  FP64 (the parity path): no bound.
+// ELBM_STEP_MIN_BLOCKS overrides.
 #ifndef ELBM_STEP_MIN_BLOCKS
 #define ELBM_STEP_MIN_BLOCKS 0
+#endif
+// D2Q9 with FP32 arithmetic runs two nodes per thread (node_collide_x2), in blocks of
+// kStepBlock / 2 threads: 8 of them per SM (at most 64 registers) for FP32 and 16-bit
+// storage, 6 (80 registers) for FP32 deviations, whose collision keeps d_i and spills at 64
+// (4096^2 shear layer: 0.190 against 0.193 ms; FP32 storage loses with 80: 0.188 against
+// 0.179).
+#ifndef ELBM_PAIR_MIN_BLOCKS
+#define ELBM_PAIR_MIN_BLOCKS 8
+#endif
+#ifndef ELBM_PAIR_MIN_BLOCKS_DEV
+#define ELBM_PAIR_MIN_BLOCKS_DEV 6
 #endif
 template <class ST>
 constexpr int step_min_blocks()
 {
     return ELBM_STEP_MIN_BLOCKS > 0 ? ELBM_STEP_MIN_BLOCKS
                                     : (sizeof(typename ST::T) != 4 ? 1
-                                       : D == 2                  ? 4
+                                       : D == 2 ? (ST::kDevCollide ? ELBM_PAIR_MIN_BLOCKS_DEV : ELBM_PAIR_MIN_BLOCKS)
                                        : sizeof(typename ST::S) == 4 ? 7 : 5);
 }
-#define ELBM_STEP_BOUNDS __launch_bounds__(kStepBlock, step_min_blocks<ST>())
+// Two-node kernels: warp w of a block takes the aligned run of kPairSpan nodes
+// [kPairSpan w, kPairSpan (w + 1)) of the block's nodes, lane l nodes l and l + 32 of
+// it.  A warp's nodes (and so its coefficient form) are then the same whatever the
+// block width, and each of its loads covers 32 consecutive nodes.
+constexpr uint32_t kPairSpan = 64;
+__device__ __forceinline__ uint32_t pair_node(uint32_t t) { return (t >> 5) * kPairSpan + (t & 31u); }
+// threads per block of the direct step kernel
+template <class ST>
+constexpr int step_threads()
+{
+    return kStepBlock / nodes_per_thread<D, ST>();
+}
+#define ELBM_STEP_BOUNDS __launch_bounds__(step_threads<ST>(), step_min_blocks<ST>())
 
 template <class ST, bool kGrid3D, bool kForce = false>
 __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
@@ -77,6 +100,68 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
                                                     CollideParams p)
 {
     using T = typename ST::T;
+    if constexpr (nodes_per_thread<D, ST>() == 2) {
+        // Two nodes per thread (pair_node); a second node past the end of the row (or of
+        // the domain) is a copy of the first, collided and not stored.
+        constexpr uint32_t H = kPairSpan / 2;
+        T fa[Q], fb[Q];
+        if constexpr (kGrid3D) {
+            const uint32_t nx = uint32_t(g.nx), ny = uint32_t(g.ny), N = uint32_t(g.N);
+            const uint32_t xa = blockIdx.x * kStepBlock + pair_node(threadIdx.x);
+            if (xa >= nx) return;
+            const bool hasb = xa + H < nx;
+            const uint32_t xb = hasb ? xa + H : xa;
+            const uint32_t y = blockIdx.y;
+            const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            auto src = [&](uint32_t x, int i) -> uint32_t {
+                const int cx = vel(D, i, 0), cy = vel(D, i, 1);
+                const uint32_t sx = cx == 1 ? (x == 0 ? nx - 1 : x - 1) : (cx == -1 ? (x == nx - 1 ? 0 : x + 1) : x);
+                const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+                return uint32_t(i) * N + sy * nx + sx;
+            };
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fa[i] = step_in<ST>(__ldg(fin + src(xa, i)), dev_ref<D, T>(i, p.dunit_f));
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fb[i] = step_in<ST>(__ldg(fin + src(xb, i)), dev_ref<D, T>(i, p.dunit_f));
+            collide2_stored<D, ST, true>(fa, fb, p);
+            if constexpr (kForce) {
+                add_force<D, T, ST::kDevCollide>(fa, p);
+                add_force<D, T, ST::kDevCollide>(fb, p);
+            }
+            const uint32_t na = y * nx + xa, nb = y * nx + xb;
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                __stcs(fout + (uint32_t(i) * N + na), step_out<ST>(fa[i], dev_ref<D, T>(i, p.dunit_f)));
+            if (hasb) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    __stcs(fout + (uint32_t(i) * N + nb), step_out<ST>(fb[i], dev_ref<D, T>(i, p.dunit_f)));
+            }
+        } else {
+            const int64_t na = (int64_t)blockIdx.x * kStepBlock + pair_node(threadIdx.x);
+            if (na >= g.N) return;
+            const bool hasb = na + H < g.N;
+            const int64_t nb = hasb ? na + H : na;
+            int x, y, z;
+            node_coords(na, g, x, y, z);
+            pull_load<D, ST, true>(fin, g, x, y, z, p.dunit_f, fa);
+            node_coords(nb, g, x, y, z);
+            pull_load<D, ST, true>(fin, g, x, y, z, p.dunit_f, fb);
+            collide2_stored<D, ST, true>(fa, fb, p);
+            if constexpr (kForce) {
+                add_force<D, T, ST::kDevCollide>(fa, p);
+                add_force<D, T, ST::kDevCollide>(fb, p);
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) __stcs(fout + (int64_t)i * g.N + na, step_out<ST>(fa[i], dev_ref<D, T>(i, p.dunit_f)));
+            if (hasb) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    __stcs(fout + (int64_t)i * g.N + nb, step_out<ST>(fb[i], dev_ref<D, T>(i, p.dunit_f)));
+            }
+        }
+        return;
+    }
     T f[Q], xd[Q]; // the stored values (deviations for deviation storage)
     int br;
     if constexpr (kGrid3D) {
@@ -501,6 +586,50 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
     diag_finish<kStepBlock>(dt, acc, s_hist);
 }
 
+// Two nodes x and x + 32 of row y of a D2Q9 domain (nx by ny, N nodes, populations
+// at in / out): pull, collide (node_collide_x2), store; a second node past the end of
+// the row is a copy of the first, collided and not stored.  Plain loads when kCoherent
+// (buffers written during the launch), else the read-only path.
+template <class ST, bool kCoherent = false>
+__device__ __forceinline__ void step2_row(const typename ST::S *in, typename ST::S *out, uint32_t nx, uint32_t ny,
+                                          uint32_t N, uint32_t xa, uint32_t y, const CollideParams &p)
+{
+    using T = typename ST::T;
+    constexpr uint32_t H = kPairSpan / 2;
+    const bool hasb = xa + H < nx;
+    const uint32_t xb = hasb ? xa + H : xa;
+    const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    auto src = [&](uint32_t x, int i) -> uint32_t {
+        const int cx = vel(D, i, 0), cy = vel(D, i, 1);
+        const uint32_t sx = cx == 1 ? (x == 0 ? nx - 1 : x - 1) : (cx == -1 ? (x == nx - 1 ? 0 : x + 1) : x);
+        const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+        return uint32_t(i) * N + sy * nx + sx;
+    };
+    auto ld = [&](uint32_t o) { return kCoherent ? in[o] : __ldg(in + o); };
+    T fa[Q], fb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fa[i] = step_in<ST>(ld(src(xa, i)), dev_ref<D, T>(i, p.dunit_f));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fb[i] = step_in<ST>(ld(src(xb, i)), dev_ref<D, T>(i, p.dunit_f));
+    collide2_stored<D, ST, true>(fa, fb, p);
+    const uint32_t na = y * nx + xa, nb = y * nx + xb;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const typename ST::S v = step_out<ST>(fa[i], dev_ref<D, T>(i, p.dunit_f));
+        if (kCoherent) out[uint32_t(i) * N + na] = v;
+        else __stcs(out + (uint32_t(i) * N + na), v);
+    }
+    if (hasb) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const typename ST::S v = step_out<ST>(fb[i], dev_ref<D, T>(i, p.dunit_f));
+            if (kCoherent) out[uint32_t(i) * N + nb] = v;
+            else __stcs(out + (uint32_t(i) * N + nb), v);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // --------------------------------------------------------------------------
 // Batched ensemble: one launch advances up to kBatchTableDomains domains.  Block
 // b is one work item, nodes x0 .. x0 + BX - 1 of one x-row of one domain; the
@@ -510,8 +639,16 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
 // offsets inside the domain).  Each domain has its own beta; everything else is the
 // single-domain step.
 // --------------------------------------------------------------------------
+#ifndef ELBM_BATCH_THREADS_PER_SM
+#define ELBM_BATCH_THREADS_PER_SM 0
+#endif
 template <class ST, int BX>
-__global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restrict__ fin,
+constexpr int batch_min_blocks()
+{
+    return ELBM_BATCH_THREADS_PER_SM > 0 ? ELBM_BATCH_THREADS_PER_SM / (BX / nodes_per_thread<D, ST>()) : 0;
+}
+template <class ST, int BX>
+__global__ void __launch_bounds__(BX / nodes_per_thread<D, ST>(), batch_min_blocks<ST, BX>()) k_step_batch(const typename ST::S *__restrict__ fin,
                                                   typename ST::S *__restrict__ fout,
                                                   const __grid_constant__ BatchTable tab, CollideParams p)
 {
@@ -523,13 +660,18 @@ __global__ void __launch_bounds__(BX) k_step_batch(const typename ST::S *__restr
     const uint32_t nx = uint32_t(dm.nx), ny = uint32_t(dm.ny), nz = uint32_t(dm.nz), xb = uint32_t(dm.xblocks);
     const uint32_t it = uint32_t(bid - tab.item0[lo]);
     const uint32_t row = it / xb;
-    const uint32_t x = (it - row * xb) * BX + threadIdx.x;
+    const uint32_t x = (it - row * xb) * BX + (nodes_per_thread<D, ST>() == 2 ? pair_node(threadIdx.x) : threadIdx.x);
     if (x >= nx) return;
     const uint32_t z = row / ny, y = row - z * ny, N = nx * ny * nz;
     p.beta = dm.beta;
     p.beta_f = dm.beta_f;
     const typename ST::S *in = fin + dm.off;
     typename ST::S *out = fout + dm.off;
+    if constexpr (nodes_per_thread<D, ST>() == 2) {
+        // two nodes per thread (D2Q9: z = 0), as in k_step
+        step2_row<ST>(in, out, nx, ny, N, x, y, p);
+        return;
+    }
     const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
@@ -577,7 +719,7 @@ __device__ __forceinline__ bool wait_count(const unsigned *cnt, unsigned target,
 }
 
 template <class ST, int BX>
-__global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typename ST::S *pop1, int cur,
+__global__ void __launch_bounds__(BX / nodes_per_thread<D, ST>()) k_step_persist(typename ST::S *pop0, typename ST::S *pop1, int cur,
                                                     int nsteps, const BatchTableDom *__restrict__ doms,
                                                     PersistPlan plan, CollideParams p, int *err)
 {
@@ -611,8 +753,9 @@ __global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typen
             // x-chunk c; one division for the first item, then counters
             uint32_t row = uint32_t(seg.y) / xb, c = uint32_t(seg.y) - row * xb;
             uint32_t z = row / ny, y = row - z * ny;
+            const uint32_t tx = nodes_per_thread<D, ST>() == 2 ? pair_node(threadIdx.x) : threadIdx.x;
             for (uint32_t w = uint32_t(seg.y); w < uint32_t(seg.z); ++w) {
-                const uint32_t x = c * BX + threadIdx.x;
+                const uint32_t x = c * BX + tx;
                 const uint32_t yc = y, zc = z;
                 if (++c == xb) { // next row
                     c = 0;
@@ -622,6 +765,10 @@ __global__ void __launch_bounds__(BX) k_step_persist(typename ST::S *pop0, typen
                     }
                 }
                 if (x >= nx) continue;
+                if constexpr (nodes_per_thread<D, ST>() == 2) {
+                    step2_row<ST, true>(in, out, nx, ny, N, x, yc, p);
+                    continue;
+                }
                 const uint32_t y = yc, z = zc;
                 const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
                 const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
@@ -903,22 +1050,22 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
     if (g.ny <= 65535 && g.nz <= 65535 && uint64_t(Q) * uint64_t(g.N) <= 0xffffffffull) {
         const dim3 grid(unsigned((g.nx + kStepBlock - 1) / kStepBlock), unsigned(g.ny), unsigned(g.nz));
         if (forced) {
-            ELBM_STORAGE_SWITCH(storage, (k_step<ST, true, true><<<grid, kStepBlock, 0, s>>>(
+            ELBM_STORAGE_SWITCH(storage, (k_step<ST, true, true><<<grid, step_threads<ST>(), 0, s>>>(
                                              static_cast<const typename ST::S *>(fin),
                                              static_cast<typename ST::S *>(fout), g, p)));
         } else {
-            ELBM_STORAGE_SWITCH(storage, (k_step<ST, true><<<grid, kStepBlock, 0, s>>>(
+            ELBM_STORAGE_SWITCH(storage, (k_step<ST, true><<<grid, step_threads<ST>(), 0, s>>>(
                                              static_cast<const typename ST::S *>(fin),
                                              static_cast<typename ST::S *>(fout), g, p)));
         }
     } else {
         if (forced) {
             ELBM_STORAGE_SWITCH(storage,
-                                (k_step<ST, false, true><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
+                                (k_step<ST, false, true><<<blocks_for(g.N, kStepBlock), step_threads<ST>(), 0, s>>>(
                                     static_cast<const typename ST::S *>(fin),
                                     static_cast<typename ST::S *>(fout), g, p)));
         } else {
-            ELBM_STORAGE_SWITCH(storage, (k_step<ST, false><<<blocks_for(g.N, kStepBlock), kStepBlock, 0, s>>>(
+            ELBM_STORAGE_SWITCH(storage, (k_step<ST, false><<<blocks_for(g.N, kStepBlock), step_threads<ST>(), 0, s>>>(
                                              static_cast<const typename ST::S *>(fin),
                                              static_cast<typename ST::S *>(fout), g, p)));
         }
@@ -951,7 +1098,7 @@ cudaError_t ELBM_CAT(launch_step_batch, ELBM_SUFFIX)(int storage, const void *fi
     const int nitems = tab.item0[tab.n];
     if (tab.n <= 0 || nitems <= 0) return cudaSuccess;
 #define ELBM_BATCH_BX(BXV)                                                                             \
-    ELBM_STORAGE_SWITCH(storage, (k_step_batch<ST, BXV><<<unsigned(nitems), BXV, 0, s>>>(               \
+    ELBM_STORAGE_SWITCH(storage, (k_step_batch<ST, BXV><<<unsigned(nitems), BXV / nodes_per_thread<D, ST>(), 0, s>>>( \
                                      static_cast<const typename ST::S *>(fin),                          \
                                      static_cast<typename ST::S *>(fout), tab, p)))
     switch (bx) {
@@ -970,7 +1117,7 @@ cudaError_t ELBM_CAT(persist_blocks_per_sm, ELBM_SUFFIX)(int storage, int bx, in
     *blocks = 0;
 #define ELBM_PERSIST_OCC(BXV)                                                                          \
     ELBM_STORAGE_SWITCH(storage, return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks,           \
-                                                                             k_step_persist<ST, BXV>, BXV, 0))
+                                                                             k_step_persist<ST, BXV>, BXV / nodes_per_thread<D, ST>(), 0))
     switch (bx) {
     case 64: ELBM_PERSIST_OCC(64); break;
     case 128: ELBM_PERSIST_OCC(128); break;
@@ -997,8 +1144,8 @@ cudaError_t ELBM_CAT(launch_step_persist, ELBM_SUFFIX)(int storage, void *pop0, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
 #define ELBM_PERSIST_BX(BXV)                                                                           \
-    cfg.blockDim = dim3(BXV);                                                                          \
-    ELBM_STORAGE_SWITCH(storage, return cudaLaunchKernelEx(&cfg, k_step_persist<ST, BXV>,               \
+    ELBM_STORAGE_SWITCH(storage, cfg.blockDim = dim3(BXV / nodes_per_thread<D, ST>());                 \
+                                 return cudaLaunchKernelEx(&cfg, k_step_persist<ST, BXV>,               \
                                                            static_cast<typename ST::S *>(pop0),        \
                                                            static_cast<typename ST::S *>(pop1), cur,   \
                                                            nsteps, doms, plan, p, err))

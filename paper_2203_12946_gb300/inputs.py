@@ -20,7 +20,8 @@ flows):
 * ``random_vortex_2d`` -- random-phase streamfunction with a Gaussian shell
   spectrum peaked at |k| = k0, u = curl psi, rescaled to a target rms speed.
 * ``population_noise`` -- multiplicative factors 1 + eps * U(-1, 1) used to push
-  equilibrium populations off equilibrium in parity tests.
+  equilibrium populations off equilibrium in parity tests (one amplitude for all
+  nodes, or one per node).
 
 Every generator takes integer node coordinates so that a sub-box of a large
 field can be regenerated exactly; ``grid`` builds the full coordinate arrays.
@@ -101,6 +102,6 @@ def random_state_2d(L, rms=0.05, seed=DEFAULT_SEED):
 
 
 def population_noise(Q, N, eps, seed=DEFAULT_SEED):
-    """Factors 1 + eps * U(-1, 1), shape (Q, N)."""
+    """Factors 1 + eps * U(-1, 1), shape (Q, N); eps a number or one amplitude per node."""
     rng = np.random.default_rng(seed)
     return 1.0 + eps * (2.0 * rng.random((Q, N)) - 1.0)

@@ -241,6 +241,43 @@ def test_fp32_series_and_exact_paths(D, dims, storage):
     assert np.max(rel[:, agree]) < 2e-6
 
 
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+@pytest.mark.parametrize("mode,b_variant", [("higher", E.ELBM_B_DERIVED), ("higher", E.ELBM_B_PRINTED),
+                                            ("lower", E.ELBM_B_DERIVED), ("lbgk", E.ELBM_B_DERIVED)])
+def test_fp32_d2q9_two_node_collision_mixed_branches(storage, mode, b_variant):
+    """D2Q9 FP32 steps collide two nodes per thread (x and x + 32), one in each lane of the
+    paired FP32 instructions.  The noise amplitude rises geometrically along x, from 1e-5
+    to 0.9, so the two nodes of a thread often take different branches (cutoff, solved,
+    clamped) and different coefficient forms; every mode and both readings of b against
+    the oracle, on a ragged width (a thread's second node past the end of its row is not
+    stored)."""
+    D, dims, beta = 2, (203, 41, 1), 0.99
+    X, Y, _ = inputs.grid(dims)
+    rho, u = inputs.taylor_green_2d(X, Y, dims[0], u0=0.05)
+    amp = 10.0 ** np.interp(X, [0, dims[0] - 1], [-5.0, np.log10(0.9)])
+    f = O.init_equilibrium(D, rho, u) * inputs.population_noise(9, X.size, amp, seed=61)
+    f0, f_in = stored(D, f, storage)
+    gm, om = MODES[mode]
+    f_gpu = gpu_run(D, dims, beta, f0, 1, storage, alpha_mode=gm, b_variant=b_variant, cutoff=True)
+    f_ora, a_ora, br_ora, _ = O.step(D, dims, f_in, beta, cutoff=True, mode=om, b_variant=b_variant,
+                                     want_alpha=True)
+    if mode != "lbgk":
+        for b, least in ((O.BRANCH_CUTOFF, 500), (O.BRANCH_SOLVED, 5000), (O.BRANCH_CLAMPED, 10)):
+            assert np.sum(br_ora == b) > least, b
+    with E.Simulation(LAT[D], dims, beta, storage=storage, alpha_mode=gm, b_variant=b_variant,
+                      cutoff=True) as sim:
+        sim.set_populations(f0)
+        _, fl = [t.cpu().numpy() for t in sim.alpha_field()]
+    f_pre = O.stream(D, dims, f_in)
+    agree = check_branches(D, f_pre, fl, br_ora, 1e-6)
+    # far from equilibrium f* = f + alpha beta (f^eq - f) cancels (to 1e-2 of f and below
+    # at the highest amplitudes), so the error is measured against the size of its terms
+    feq = O.init_equilibrium(D, *O.moments_field(D, f_pre))
+    scale = f_pre + 2.5 * np.abs(feq - f_pre)
+    err = np.abs(f_gpu - f_ora) / scale
+    assert np.max(err[:, agree]) < 2e-6
+
+
 @pytest.mark.parametrize("D,dims", [(2, (131, 29, 1)), (3, (21, 13, 9))])
 @pytest.mark.parametrize("storage", ["f32", "f32dev"])
 def test_fp32_iterate1_mode(D, dims, storage):
