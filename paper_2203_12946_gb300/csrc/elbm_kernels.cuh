@@ -639,13 +639,25 @@ __device__ __forceinline__ void step2_row(const typename ST::S *in, typename ST:
 // offsets inside the domain).  Each domain has its own beta; everything else is the
 // single-domain step.
 // --------------------------------------------------------------------------
+// Resident threads per SM requested from the register allocator for the batched ensemble
+// kernel (0: no bound).  Two-node D2Q9 kernels: 1024 (at most 64 registers; 74.7 against
+// 65.7 GLUPS on the 64-domain ensemble with the 80 the compiler picks unbounded), 768 for
+// FP32 deviations (80 registers); one node per thread: no bound.  The persistent kernel
+// keeps the compiler's choice (bounded to 64 registers it spills: 60.2 against 62.6 GLUPS).
 #ifndef ELBM_BATCH_THREADS_PER_SM
 #define ELBM_BATCH_THREADS_PER_SM 0
 #endif
+template <class ST>
+constexpr int batch_threads_per_sm()
+{
+    return ELBM_BATCH_THREADS_PER_SM > 0 ? ELBM_BATCH_THREADS_PER_SM
+           : nodes_per_thread<D, ST>() == 2 ? (ST::kDevCollide ? 768 : 1024)
+                                            : 0;
+}
 template <class ST, int BX>
 constexpr int batch_min_blocks()
 {
-    return ELBM_BATCH_THREADS_PER_SM > 0 ? ELBM_BATCH_THREADS_PER_SM / (BX / nodes_per_thread<D, ST>()) : 0;
+    return batch_threads_per_sm<ST>() / (BX / nodes_per_thread<D, ST>());
 }
 template <class ST, int BX>
 __global__ void __launch_bounds__(BX / nodes_per_thread<D, ST>(), batch_min_blocks<ST, BX>()) k_step_batch(const typename ST::S *__restrict__ fin,
