@@ -30,6 +30,10 @@ struct elbm {
     int cur = 0; // buffer holding the current state
     double *stage = nullptr;
     size_t stage_bytes = 0;
+    // host transfers of FP64 fields: a copy stream and events, so that the copies of one
+    // node range overlap the kernel of another (created with the staging buffer)
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev[1 + 8] = {};
     DiagAcc *acc = nullptr;
     int *err_word = nullptr; // device: ELBM_ERR_TIMEOUT when a bounded device wait expired
     int num_sms = 0;
@@ -119,8 +123,19 @@ int ensure_populations(elbm_t *h)
     return ELBM_OK;
 }
 
+// The host transfers of elbm_init_equilibrium and elbm_moments are cut into
+// kStageChunks node ranges (of at least 2^20 nodes), pipelined on two streams.
+constexpr int kStageChunks = 8;
+int stage_chunks(int64_t N) { return N >= (int64_t(kStageChunks) << 20) ? kStageChunks : 1; }
+
 int ensure_stage(elbm_t *h, size_t bytes)
 {
+    if (!h->copy) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking);
+        for (int k = 0; k < 1 + kStageChunks && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate/cudaEventCreate(staging)");
+    }
     if (h->stage_bytes >= bytes) return ELBM_OK;
     if (h->stage) {
         cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -290,6 +305,9 @@ void elbm_destroy(elbm_t *h)
     cudaFree(h->stage);
     cudaFree(h->acc);
     cudaFree(h->err_word);
+    for (cudaEvent_t ev : h->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (h->copy) cudaStreamDestroy(h->copy);
     delete h;
 }
 
@@ -343,28 +361,36 @@ int elbm_init_equilibrium(elbm_t *h, const double *rho, const double *u, int whe
     int st = ensure_populations(h);
     if (st != ELBM_OK) return st;
     const int64_t N = h->g.N;
-    const double *drho = rho, *du = u;
+    cudaError_t e;
     if (where == ELBM_MEM_HOST) {
         const size_t need = size_t(N) * (1 + h->D) * sizeof(double);
         if ((st = ensure_stage(h, need)) != ELBM_OK) return st;
-        double *srho = h->stage, *su = h->stage + N;
-        cudaError_t e;
-        if (rho) {
-            e = cudaMemcpyAsync(srho, rho, size_t(N) * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: copy rho");
-            drho = srho;
+        double *srho = rho ? h->stage : nullptr, *su = h->stage + N;
+        // the copies start after the work already queued on the handle's stream; the
+        // kernel of each node range waits for that range's copies
+        e = cudaEventRecord(h->ev[0], h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy, h->ev[0], 0);
+        const int C = stage_chunks(N);
+        for (int c = 0; c < C && e == cudaSuccess; ++c) {
+            const int64_t n0 = N * c / C, cnt = N * (c + 1) / C - n0;
+            if (rho) e = cudaMemcpyAsync(srho + n0, rho + n0, size_t(cnt) * sizeof(double), cudaMemcpyHostToDevice,
+                                         h->copy);
+            for (int a = 0; a < h->D && e == cudaSuccess; ++a)
+                e = cudaMemcpyAsync(su + a * N + n0, u + a * N + n0, size_t(cnt) * sizeof(double),
+                                    cudaMemcpyHostToDevice, h->copy);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev[1 + c], h->copy);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev[1 + c], 0);
+            if (e == cudaSuccess)
+                e = ELBM_BY_LATTICE(h, launch_init, h->opts.storage, srho, su, h->pop[0], h->g, h->opts.rho0,
+                                    h->opts.rho0, n0, cnt, h->stream);
         }
-        e = cudaMemcpyAsync(su, u, size_t(N) * h->D * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: copy u");
-        du = su;
-    }
-    cudaError_t e = ELBM_BY_LATTICE(h, launch_init, h->opts.storage, drho, du, h->pop[0], h->g, h->opts.rho0,
-                                    h->opts.rho0, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: kernel launch");
-    if (where == ELBM_MEM_HOST) {
         // the caller may reuse its host arrays as soon as we return
-        e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: synchronize");
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: copy, kernel or synchronize");
+    } else {
+        e = ELBM_BY_LATTICE(h, launch_init, h->opts.storage, rho, u, h->pop[0], h->g, h->opts.rho0, h->opts.rho0,
+                            0, N, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_init_equilibrium: kernel launch");
     }
     h->cur = 0;
     h->steps = 0;
@@ -397,29 +423,34 @@ int elbm_moments(elbm_t *h, double *rho_out, double *u_out, int where)
     if (!rho_out && !u_out) return ELBM_OK;
     DeviceGuard guard(h->opts.device);
     const int64_t N = h->g.N;
-    double *drho = rho_out, *du = u_out;
     int st;
     if (where == ELBM_MEM_HOST) {
         if ((st = ensure_stage(h, size_t(N) * (1 + h->D) * sizeof(double))) != ELBM_OK) return st;
-        drho = rho_out ? h->stage : nullptr;
-        du = u_out ? h->stage + N : nullptr;
-    }
-    cudaError_t e = ELBM_BY_LATTICE(h, launch_moments, h->opts.storage, h->pop[h->cur], h->g, h->opts.rho0, drho,
-                                    du, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: kernel launch");
-    if (where == ELBM_MEM_HOST) {
-        if (rho_out) {
-            e = cudaMemcpyAsync(rho_out, drho, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: copy rho");
+        double *drho = rho_out ? h->stage : nullptr, *du = u_out ? h->stage + N : nullptr;
+        // the copies of each node range wait for that range's kernel
+        const int C = stage_chunks(N);
+        cudaError_t e = cudaSuccess;
+        for (int c = 0; c < C && e == cudaSuccess; ++c) {
+            const int64_t n0 = N * c / C, cnt = N * (c + 1) / C - n0;
+            e = ELBM_BY_LATTICE(h, launch_moments, h->opts.storage, h->pop[h->cur], h->g, h->opts.rho0, drho, du,
+                                n0, cnt, h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev[1 + c], h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy, h->ev[1 + c], 0);
+            if (rho_out && e == cudaSuccess)
+                e = cudaMemcpyAsync(rho_out + n0, drho + n0, size_t(cnt) * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->copy);
+            for (int a = 0; u_out && a < h->D && e == cudaSuccess; ++a)
+                e = cudaMemcpyAsync(u_out + a * N + n0, du + a * N + n0, size_t(cnt) * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->copy);
         }
-        if (u_out) {
-            e = cudaMemcpyAsync(u_out, du, size_t(N) * h->D * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: copy u");
-        }
-        e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: synchronize");
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: kernel, copy or synchronize");
         return check_device_flag(h, "elbm_moments");
     }
+    cudaError_t e = ELBM_BY_LATTICE(h, launch_moments, h->opts.storage, h->pop[h->cur], h->g, h->opts.rho0, rho_out,
+                                    u_out, 0, N, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "elbm_moments: kernel launch");
     return ELBM_OK;
 }
 

@@ -490,9 +490,9 @@ int elbm_batch_init_equilibrium(elbm_batch_t *b, int domain, const double *rho, 
     for (int k = 0; k < 2; ++k) {
         void *f = static_cast<char *>(b->pop[k]) + size_t(dm.off) * b->elem;
         e = b->D == 2 ? eelbm::launch_init_d2q9(b->opts.storage, drho, du, f, geom_of(dm), b->opts.rho0, b->opts.rho0,
-                                                b->stream)
+                                                0, dm.N, b->stream)
                       : eelbm::launch_init_d3q27(b->opts.storage, drho, du, f, geom_of(dm), b->opts.rho0,
-                                                 b->opts.rho0, b->stream);
+                                                 b->opts.rho0, 0, dm.N, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_init_equilibrium: kernel launch");
     }
     if (where == ELBM_MEM_HOST) {
@@ -721,9 +721,9 @@ int elbm_batch_moments(elbm_batch_t *b, int domain, double *rho_out, double *u_o
     }
     const void *f = static_cast<const char *>(b->pop[b->cur]) + size_t(dm.off) * b->elem;
     cudaError_t e = b->D == 2 ? eelbm::launch_moments_d2q9(b->opts.storage, f, geom_of(dm), b->opts.rho0, drho, du,
-                                                           b->stream)
+                                                           0, dm.N, b->stream)
                               : eelbm::launch_moments_d3q27(b->opts.storage, f, geom_of(dm), b->opts.rho0, drho,
-                                                            du, b->stream);
+                                                            du, 0, dm.N, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "elbm_batch_moments: kernel launch");
     if (where == ELBM_MEM_HOST) {
         if (rho_out) e = cudaMemcpyAsync(rho_out, drho, size_t(dm.N) * sizeof(double), cudaMemcpyDeviceToHost,

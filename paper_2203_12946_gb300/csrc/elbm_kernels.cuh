@@ -6,7 +6,7 @@
 //              fstar_def, path length of Sec. III / Appendix C-D), one node per
 //              thread, ping-pong buffers
 //   k_init     f = f^eq(rho, u) (Sec. I equilibrium, FP64, rounded to storage)
-//   k_moments  rho and u of the stored state (FP64)
+//   k_moments  rho and u of the stored state (FP64; exact fixed-point sums of FP32 values)
 //   k_alpha    path length of the next collision (no write-back)
 //   k_diag     domain reductions: mass, momentum, H (Eq. hdef), alpha statistics
 //              and per-node H[f*] - H[f] (Eq. deltaH3) in FP64; warp shuffles,
@@ -203,7 +203,11 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
     }
 }
 
-// FP64 equilibrium from rho and u (same product form as node_collide).
+// FP64 equilibrium from rho and u (same product form as node_collide).  Per axis
+// phi(-1) = Y den / (6 num) and phi(+1) = Y num / (6 den); with kOneDiv they share one
+// division, r = Y / (6 num den), phi(-1) = r den^2, phi(+1) = r num^2 (a few FP64 ulp
+// apart: used where the result is rounded to FP32 or below).
+template <bool kOneDiv>
 __device__ __forceinline__ void equilibrium64(double rho, const double (&u)[3], double (&feq)[Q])
 {
     double phi[3][3];
@@ -212,9 +216,15 @@ __device__ __forceinline__ void equilibrium64(double rho, const double (&u)[3], 
         const double s = sqrt(1.0 + 3.0 * u[a] * u[a]);
         const double Y = 2.0 - s;
         const double num = 2.0 * u[a] + s, den = 1.0 - u[a];
-        phi[a][0] = Y * den / (6.0 * num);
+        if (kOneDiv) {
+            const double r = Y / (6.0 * num * den);
+            phi[a][0] = r * den * den;
+            phi[a][2] = r * num * num;
+        } else {
+            phi[a][0] = Y * den / (6.0 * num);
+            phi[a][2] = Y * num / (6.0 * den);
+        }
         phi[a][1] = Y * (4.0 / 6.0);
-        phi[a][2] = Y * num / (6.0 * den);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -225,33 +235,188 @@ __device__ __forceinline__ void equilibrium64(double rho, const double (&u)[3], 
     }
 }
 
+// Double-length FP32 arithmetic ("double-float": a value hi + lo with |lo| <= ulp(hi)/2):
+// Dekker's product with a fused multiply-add for the exact error of hi * hi, Knuth's
+// two-sum and Dekker's fast two-sum for additions, and one Newton correction on the FP32
+// square root and quotient.  About 44 significant bits, at FP32 instruction rates.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_from_double(double x)
+{
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - double(h))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = a.hi + b.hi, bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb); // two-sum error
+    return df_fast_two_sum(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_mulf(DF a, float b)
+{
+    const float p = a.hi * b;
+    return df_fast_two_sum(p, fmaf(a.lo, b, fmaf(a.hi, b, -p)));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b)
+{
+    const float q = a.hi / b.hi;
+    const DF qb = df_mulf(b, q);
+    const float r = ((a.hi - qb.hi) - qb.lo) + a.lo; // a - q b, to the first order
+    return df_fast_two_sum(q, r / b.hi);
+}
+__device__ __forceinline__ DF df_sqrt(DF a)
+{
+    const float r = sqrtf(a.hi);
+    const float e = fmaf(-r, r, a.hi) + a.lo; // a - r^2
+    return df_fast_two_sum(r, e / (2.0f * r));
+}
+
+// The equilibrium of equilibrium64<true> in double-float: f^eq rounded once to FP32
+// (|stored - f^eq| <= half an FP32 ulp + 2^-43 f^eq), without the FP64 pipe.
+__device__ __forceinline__ void equilibrium_df(double rho, const double (&u)[3], float (&feq)[Q])
+{
+    constexpr double kTwoThirds = 2.0 / 3.0;
+    const DF two3 = {float(kTwoThirds), float(kTwoThirds - double(float(kTwoThirds)))};
+    DF phi[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const DF U = df_from_double(u[a]);
+        const DF S = df_sqrt(df_add({1.0f, 0.0f}, df_mulf(df_mul(U, U), 3.0f)));
+        const DF Y = df_add({2.0f, 0.0f}, {-S.hi, -S.lo});
+        const DF num = df_add({2.0f * U.hi, 2.0f * U.lo}, S), den = df_add({1.0f, 0.0f}, {-U.hi, -U.lo});
+        const DF r = df_div(Y, df_mulf(df_mul(num, den), 6.0f));
+        phi[a][0] = df_mul(r, df_mul(den, den));
+        phi[a][1] = df_mul(Y, two3);
+        phi[a][2] = df_mul(r, df_mul(num, num));
+    }
+    const DF R = df_from_double(rho);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        DF v = R;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v = df_mul(v, phi[a][vel(D, i, a) + 1]);
+        feq[i] = v.hi;
+    }
+}
+
+// f = f^eq(rho, u) for the nodes n0 .. n0 + count - 1 (SoA with stride g.N).
 template <class ST>
 __global__ void __launch_bounds__(kAuxBlock) k_init(const double *__restrict__ rho,
                                                    const double *__restrict__ u,
                                                    typename ST::S *__restrict__ f, Geometry g,
-                                                   double rho_uniform, double rho0)
+                                                   double rho_uniform, double rho0, int64_t n0, int64_t count)
 {
-    const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
-    if (n >= g.N) return;
+    const int64_t k = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+    if (k >= count) return;
+    const int64_t n = n0 + k;
     double un[3] = {0.0, 0.0, 0.0}, feq[Q];
 #pragma unroll
     for (int a = 0; a < D; ++a) un[a] = u[(int64_t)a * g.N + n];
-    equilibrium64(rho ? rho[n] : rho_uniform, un, feq);
+    if constexpr (!ST::kDev && sizeof(typename ST::S) == 4) {
+        // FP32 populations: the equilibrium in double-float, rounded once
+        float fe[Q];
+        equilibrium_df(rho ? rho[n] : rho_uniform, un, fe);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[(int64_t)i * g.N + n] = fe[i];
+        return;
+    }
+    equilibrium64<sizeof(typename ST::S) < 8>(rho ? rho[n] : rho_uniform, un, feq);
     const double R = double(dev_unit<D>(rho0));
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[(int64_t)i * g.N + n] = ST::store64(feq[i], weight_k(D, i) * R);
 }
 
+// Exact sums of FP32 values in 64-bit fixed point.  A finite FP32 value is m 2^(e - 150),
+// e its biased exponent (taken as 1 for subnormals) and m its significand (with the hidden
+// bit for normal numbers).  Scaled to a common exponent E0 = e_max - 33 of the values summed,
+// each becomes an integer below 2^57 (a value more than 2^33 below the largest loses its low
+// bits), 32 of them add without overflow, and the integer sum converts to FP64 with one
+// rounding (none while it stays below 2^53).
+__device__ __forceinline__ int f32_expo(float v)
+{
+    const int e = int((__float_as_uint(v) >> 23) & 0xffu);
+    return e ? e : 1;
+}
+__device__ __forceinline__ long long f32_fixed(float v, int E0)
+{
+    const uint32_t b = __float_as_uint(v);
+    const int e = int((b >> 23) & 0xffu);
+    const uint32_t m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int sh = (e ? e : 1) - E0;
+    const unsigned long long mag =
+        sh >= 0 ? (unsigned long long)m << sh : (sh > -24 ? (unsigned long long)(m >> -sh) : 0ull);
+    return (b >> 31) ? -(long long)mag : (long long)mag;
+}
+__device__ __forceinline__ double fixed_to_f64(long long q, int E0)
+{
+    return double(q) * __longlong_as_double((long long)(E0 - 150 + 1023) << 52);
+}
+
+// rho and u of the stored state (FP64) for the nodes n0 .. n0 + count - 1.  FP64 storage
+// sums in FP64.  The FP32-arithmetic storages hold FP32 values (populations, or deviations
+// d_i of the reference c_i = k_i R with sum_i c_i = 6^D R and sum_i c_i c_i = 0): their sums
+// are taken exactly in fixed point (f32_fixed) and rounded once to FP64, the result the FP64
+// sums of the same values give whenever those are exact, without the FP64 pipe's rate; a
+// node holding a value that is not finite is summed in FP64.
 template <class ST>
 __global__ void __launch_bounds__(kAuxBlock) k_moments(const typename ST::S *__restrict__ f,
                                                       Geometry g, double rho0,
                                                       double *__restrict__ rho_out,
-                                                      double *__restrict__ u_out)
+                                                      double *__restrict__ u_out, int64_t n0, int64_t count)
 {
-    const int64_t n = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
-    if (n >= g.N) return;
-    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    const int64_t k = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+    if (k >= count) return;
+    const int64_t n = n0 + k;
     const double R = double(dev_unit<D>(rho0));
+    if constexpr (sizeof(typename ST::T) == 4) {
+        float v[Q];
+        int emax = 1;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            v[i] = ST::raw(f[(int64_t)i * g.N + n]);
+            emax = max(emax, f32_expo(v[i]));
+        }
+        const float Rf = dev_unit<D>(rho0);
+        if (ST::kDev) emax = max(emax, f32_expo(Rf) + 8); // 6^D R < 2^8 R
+        if (emax < 255) {
+            const int E0 = emax - 33;
+            long long r = 0, j[3] = {0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const long long q = f32_fixed(v[i], E0);
+                r += q;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    if (vel(D, i, a) == 1) j[a] += q;
+                    if (vel(D, i, a) == -1) j[a] -= q;
+                }
+            }
+            if (ST::kDev) r += f32_fixed(Rf, E0) * (Q == 9 ? 36 : 216);
+            const double rho = fixed_to_f64(r, E0);
+            if (rho_out) rho_out[n] = rho;
+            if (u_out) {
+                const double ir = 1.0 / rho;
+#pragma unroll
+                for (int a = 0; a < D; ++a) u_out[(int64_t)a * g.N + n] = fixed_to_f64(j[a], E0) * ir;
+            }
+            return;
+        }
+    }
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const double v = ST::load64(f[(int64_t)i * g.N + n], weight_k(D, i) * R);
@@ -1223,23 +1388,23 @@ cudaError_t ELBM_CAT(launch_equilibrium_vjp, ELBM_SUFFIX)(int storage, const dou
 
 cudaError_t ELBM_CAT(launch_init, ELBM_SUFFIX)(int storage, const double *rho, const double *u,
                                                void *f, const Geometry &g, double rho_uniform,
-                                               double rho0, cudaStream_t s)
+                                               double rho0, int64_t n0, int64_t count, cudaStream_t s)
 {
     using namespace ELBM_SUFFIX;
-    if (g.N == 0) return cudaSuccess;
-    ELBM_STORAGE_SWITCH(storage, (k_init<ST><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
-                                     rho, u, static_cast<typename ST::S *>(f), g, rho_uniform, rho0)));
+    if (count <= 0) return cudaSuccess;
+    ELBM_STORAGE_SWITCH(storage, (k_init<ST><<<blocks_for(count, kAuxBlock), kAuxBlock, 0, s>>>(
+                                     rho, u, static_cast<typename ST::S *>(f), g, rho_uniform, rho0, n0, count)));
     return cudaGetLastError();
 }
 
 cudaError_t ELBM_CAT(launch_moments, ELBM_SUFFIX)(int storage, const void *f, const Geometry &g,
                                                   double rho0, double *rho_out, double *u_out,
-                                                  cudaStream_t s)
+                                                  int64_t n0, int64_t count, cudaStream_t s)
 {
     using namespace ELBM_SUFFIX;
-    if (g.N == 0) return cudaSuccess;
-    ELBM_STORAGE_SWITCH(storage, (k_moments<ST><<<blocks_for(g.N, kAuxBlock), kAuxBlock, 0, s>>>(
-                                     static_cast<const typename ST::S *>(f), g, rho0, rho_out, u_out)));
+    if (count <= 0) return cudaSuccess;
+    ELBM_STORAGE_SWITCH(storage, (k_moments<ST><<<blocks_for(count, kAuxBlock), kAuxBlock, 0, s>>>(
+                                     static_cast<const typename ST::S *>(f), g, rho0, rho_out, u_out, n0, count)));
     return cudaGetLastError();
 }
 

@@ -96,9 +96,10 @@ __host__ __device__ inline double from_ordered_bits(unsigned long long o)
     bool rows_kernel_applies_##SUFFIX(int storage, const Geometry &g);                               \
     cudaError_t launch_init_##SUFFIX(int storage, const double *rho, const double *u, void *f,      \
                                      const Geometry &g, double rho_uniform, double rho0,             \
-                                     cudaStream_t s);                                                \
+                                     int64_t n0, int64_t count, cudaStream_t s);                     \
     cudaError_t launch_moments_##SUFFIX(int storage, const void *f, const Geometry &g, double rho0, \
-                                        double *rho_out, double *u_out, cudaStream_t s);            \
+                                        double *rho_out, double *u_out, int64_t n0, int64_t count,  \
+                                        cudaStream_t s);                                            \
     cudaError_t launch_alpha_##SUFFIX(int storage, const void *f, const Geometry &g,                \
                                       const CollideParams &p, double *alpha_out, uint8_t *flags,    \
                                       double *nut_out, cudaStream_t s);                              \

@@ -497,8 +497,51 @@ def test_init_and_moments(storage):
     else:
         tol = 1e-15 if storage == "f64" else 6e-8
         assert np.max(np.abs(f - f_o) / f_o) < tol
+    if storage == "f32":
+        # rounded once from a ~44-bit value: the FP32 rounding of the oracle's f^eq, but
+        # where f^eq lies within ~2^-43 of a rounding midpoint (none expected here)
+        assert np.mean(f == f_o.astype(np.float32).astype(np.float64)) > 0.9999
     r_o, u_o = O.moments_field(3, f)
     assert np.max(np.abs(r_g - r_o)) < 1e-14 and np.max(np.abs(u_g - u_o)) < 1e-14
+
+
+@pytest.mark.parametrize("storage", ["f32", "f32dev", "f16dev"])
+def test_moments_are_exact_sums_of_the_stored_values(storage):
+    """elbm_moments sums the stored FP32 values exactly and rounds once to FP64: rho and
+    the momentum equal math.fsum of the populations (the correctly rounded exact sums), u
+    their quotient to two FP64 ulp, on populations spread over 2^-28 .. 1 and of both signs;
+    a node holding a non-finite value gives non-finite moments."""
+    import math
+
+    D, dims = 3, (16, 5, 3)
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(29)
+    mag = 2.0 ** rng.uniform(-28, 0, size=(27, N))
+    raw = (mag * np.where(rng.random((27, N)) < 0.2, -1.0, 1.0)).astype(np.float32)
+    if storage == "f16dev":
+        raw = (raw * 1e-2).astype(np.float16)
+    raw[:, 5] = 0.0
+    with E.Simulation(E.ELBM_D3Q27, dims, 0.9, storage=storage) as sim:
+        sim.set_populations(raw)
+        f = populations(3, sim.get_populations(), storage) if storage != "f16dev" else (
+            dev_ref(3)[:, None] + sim.get_populations().astype(np.float64))
+        r_g, u_g = [t.cpu().numpy() for t in sim.moments()]
+        bad = raw.copy()
+        bad[4, 7] = np.inf
+        sim.set_populations(bad)
+        r_b, u_b = [t.cpu().numpy() for t in sim.moments()]
+    c, _ = O.lattice(3)
+    for n in range(N):
+        col = [float(v) for v in f[:, n]]
+        rho = math.fsum(col)
+        assert r_g[n] == rho, n
+        if rho == 0.0:  # the all-zero node (FP32 storage): u = 0/0
+            continue
+        for a in range(3):
+            j = math.fsum(c[i, a] * col[i] for i in range(27))
+            assert abs(u_g[a, n] - j / rho) <= 2 * np.spacing(abs(j / rho)) + 1e-300, (n, a)
+    assert not np.isfinite(r_b[7]) or not np.all(np.isfinite(u_b[:, 7]))
+    assert np.all(np.isfinite(r_b[np.arange(N) != 7]))
 
 
 def test_diagnostics_against_oracle():
