@@ -199,10 +199,14 @@ int elbm_bind_buffers(elbm_t *h, void *pop_a, void *pop_b, size_t bytes);
 int elbm_set_stream(elbm_t *h, void *stream);
 
 /* Initial state f = f^eq(rho, u) at every node (Sec. I equilibrium), computed
- * in FP64 and rounded to the storage type.  rho: N doubles (NULL = uniform
- * rho0); u: D*N doubles, u[a*N + n].  where = ELBM_MEM_DEVICE or ELBM_MEM_HOST
- * (host arrays are copied through a library-owned staging buffer).  Resets
- * the step counter.  Errors: ELBM_ERR_ARG (u NULL, bad where), ELBM_ERR_CUDA. */
+ * in FP64 (for FP32 storage in double-length FP32 arithmetic of ~44 bits) and
+ * rounded once to the storage type.  rho: N doubles (NULL = uniform rho0); u:
+ * D*N doubles, u[a*N + n].  where = ELBM_MEM_DEVICE or ELBM_MEM_HOST (host
+ * arrays are copied through a library-owned staging buffer, in node ranges
+ * that overlap the copies with the computation; the first host call creates
+ * the buffer, a copy stream and its events).  Host inputs synchronise the
+ * stream: the caller may reuse its arrays on return.  Resets the step
+ * counter.  Errors: ELBM_ERR_ARG (u NULL, bad where), ELBM_ERR_CUDA. */
 int elbm_init_equilibrium(elbm_t *h, const double *rho, const double *u, int where);
 
 /* Advances the state by n >= 0 time steps (one fused pull-stream + collide
@@ -213,9 +217,11 @@ int elbm_init_equilibrium(elbm_t *h, const double *rho, const double *u, int whe
  * ELBM_ERR_TIMEOUT by the next synchronising call. */
 int elbm_step(elbm_t *h, int64_t n);
 
-/* rho and u of the current (post-collision) state at every node, computed in
- * FP64 from the stored populations.  rho_out: N doubles (may be NULL); u_out:
- * D*N doubles (may be NULL).  Host outputs synchronise the stream. */
+/* rho and u of the current (post-collision) state at every node, from the
+ * stored populations: rho and rho u are their exact sums rounded once to FP64
+ * (FP64 storage: FP64 sums), u = (rho u) (1/rho).  rho_out: N doubles (may be
+ * NULL); u_out: D*N doubles (may be NULL).  Host outputs are copied in node
+ * ranges behind the computation and synchronise the stream. */
 int elbm_moments(elbm_t *h, double *rho_out, double *u_out, int where);
 
 /* Per-node path length that the NEXT collision will apply (the current state
