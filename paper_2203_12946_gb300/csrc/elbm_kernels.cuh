@@ -871,17 +871,19 @@ __global__ void __launch_bounds__(BX / nodes_per_thread<D, ST>(), batch_min_bloc
 
 // --------------------------------------------------------------------------
 // Persistent ensemble: one cooperative launch advances every domain by nsteps.
-// Block b owns a fixed run of work items (plan.segs, balanced on the host; items
-// numbered inside their domain, located by division as in k_step_batch) and
-// steps it nsteps times.  Domains are independent, so a block waits only for the
-// other owners of the same domain: before step t on domain d, until cnt[d] has
-// counted t steps of each of its owners (release: stores, barrier, fence, atomic
-// add; acquire: bounded spin, fence, barrier).  Populations are read with plain
-// coherent loads, not through the read-only path, since the buffers change during
-// the launch; offsets inside a domain are 32-bit (Q N < 2^32 per domain, checked
-// when the batch is created).  Every wait is bounded (kWaitLimitNs of
-// %globaltimer, also abandoned once another block has flagged an error): on
-// expiry the block records ELBM_ERR_TIMEOUT in *err and returns.
+// Blocks draw tickets in order from one counter; ticket k is chunk k mod M of step
+// k / M (plan.chunks: runs of work items inside one domain, numbered within it and
+// located by division as in k_step_batch).  Domains are independent, so before step
+// t on domain d a block waits only until cnt[d] has counted every chunk of d at step
+// t - 1 (release: stores, barrier, fence, atomic add; acquire: bounded spin, fence,
+// barrier).  The chunks it waits for hold smaller tickets, so the smallest unfinished
+// ticket never waits and the launch cannot deadlock; idle blocks take the next chunk
+// at once, which balances the domains as the hardware scheduler does for separate
+// launches.  Populations are read with plain coherent loads, not through the read-only
+// path, since the buffers change during the launch; offsets inside a domain are 32-bit
+// (Q N < 2^32 per domain, checked when the batch is created).  Every wait is bounded
+// (kWaitLimitNs of %globaltimer, also abandoned once another block has flagged an
+// error): on expiry the block records ELBM_ERR_TIMEOUT in *err and returns.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ bool wait_count(const unsigned *cnt, unsigned target, const int *err)
 {
@@ -902,75 +904,79 @@ __global__ void __launch_bounds__(BX / nodes_per_thread<D, ST>()) k_step_persist
 {
     using T = typename ST::T;
     using S = typename ST::S;
+    __shared__ unsigned s_ticket;
     __shared__ int s_ok;
-    const int s0 = plan.seg_off[blockIdx.x], s1 = plan.seg_off[blockIdx.x + 1];
-    for (int t = 0; t < nsteps; ++t) {
-        const bool odd = ((cur + t) & 1) != 0;
+    const unsigned M = plan.nchunks, total = unsigned(nsteps) * M; // below 2^32 (host)
+    const uint32_t tx = nodes_per_thread<D, ST>() == 2 ? pair_node(threadIdx.x) : threadIdx.x;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(plan.ticket, 1u);
+        __syncthreads();
+        const unsigned tk = s_ticket;
+        if (tk >= total) return;
+        const unsigned t = tk / M;
+        const int4 seg = plan.chunks[tk - t * M];
+        if (t > 0) {
+            if (threadIdx.x == 0) {
+                s_ok = wait_count(plan.cnt + seg.x, t * plan.owners[seg.x], err);
+                if (!s_ok) atomicExch(err, ELBM_ERR_TIMEOUT);
+                __threadfence();
+            }
+            __syncthreads();
+            if (!s_ok) return;
+        }
+        const bool odd = ((unsigned(cur) + t) & 1u) != 0;
         const S *fin = odd ? pop1 : pop0;
         S *fout = odd ? pop0 : pop1;
-        for (int sg = s0; sg < s1; ++sg) {
-            const int4 seg = plan.segs[sg];
-            if (t > 0) {
-                if (threadIdx.x == 0) {
-                    s_ok = wait_count(plan.cnt + seg.x, unsigned(t) * plan.owners[seg.x], err);
-                    if (!s_ok) atomicExch(err, ELBM_ERR_TIMEOUT);
-                    __threadfence();
+        const BatchTableDom dm = doms[seg.x];
+        p.beta = dm.beta;
+        p.beta_f = dm.beta_f;
+        const uint32_t nx = uint32_t(dm.nx), ny = uint32_t(dm.ny), nz = uint32_t(dm.nz), N = nx * ny * nz;
+        const uint32_t xb = uint32_t(dm.xblocks);
+        const S *in = fin + dm.off;
+        S *out = fout + dm.off;
+        // the chunk's work items: row-major (z, y), then the x-chunk c; one division for
+        // the first item, then counters
+        uint32_t row = uint32_t(seg.y) / xb, c = uint32_t(seg.y) - row * xb;
+        uint32_t z = row / ny, y = row - z * ny;
+        for (uint32_t w = uint32_t(seg.y); w < uint32_t(seg.z); ++w) {
+            const uint32_t x = c * BX + tx;
+            const uint32_t yc = y, zc = z;
+            if (++c == xb) { // next row
+                c = 0;
+                if (++y == ny) {
+                    y = 0;
+                    ++z;
                 }
-                __syncthreads();
-                if (!s_ok) return;
             }
-            const BatchTableDom dm = doms[seg.x];
-            p.beta = dm.beta;
-            p.beta_f = dm.beta_f;
-            const uint32_t nx = uint32_t(dm.nx), ny = uint32_t(dm.ny), nz = uint32_t(dm.nz), N = nx * ny * nz;
-            const uint32_t xb = uint32_t(dm.xblocks);
-            const S *in = fin + dm.off;
-            S *out = fout + dm.off;
-            // the segment's work items, numbered inside the domain: row-major (z, y), then the
-            // x-chunk c; one division for the first item, then counters
-            uint32_t row = uint32_t(seg.y) / xb, c = uint32_t(seg.y) - row * xb;
-            uint32_t z = row / ny, y = row - z * ny;
-            const uint32_t tx = nodes_per_thread<D, ST>() == 2 ? pair_node(threadIdx.x) : threadIdx.x;
-            for (uint32_t w = uint32_t(seg.y); w < uint32_t(seg.z); ++w) {
-                const uint32_t x = c * BX + tx;
-                const uint32_t yc = y, zc = z;
-                if (++c == xb) { // next row
-                    c = 0;
-                    if (++y == ny) {
-                        y = 0;
-                        ++z;
-                    }
-                }
-                if (x >= nx) continue;
-                if constexpr (nodes_per_thread<D, ST>() == 2) {
-                    step2_row<ST, true>(in, out, nx, ny, N, x, yc, p);
-                    continue;
-                }
-                const uint32_t y = yc, z = zc;
-                const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-                const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-                const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-                T f[Q], xd[Q];
-                auto src = [&](int i) -> uint32_t {
-                    const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
-                    const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
-                    const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
-                    const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
-                    return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
-                };
+            if (x >= nx) continue;
+            if constexpr (nodes_per_thread<D, ST>() == 2) {
+                step2_row<ST, true>(in, out, nx, ny, N, x, yc, p);
+                continue;
+            }
+            const uint32_t y = yc, z = zc;
+            const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+            const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            const uint32_t zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+            T f[Q], xd[Q];
+            auto src = [&](int i) -> uint32_t {
+                const int cx = vel(D, i, 0), cy = vel(D, i, 1), cz = D == 3 ? vel(D, i, 2) : 0;
+                const uint32_t sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+                const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+                const uint32_t sz = cz == 1 ? zm : (cz == -1 ? zp : z);
+                return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
+            };
 #pragma unroll
-                for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(in[src(i)], dev_ref<D, T>(i, p.dunit_f));
-                int br;
-                collide_stored<D, ST, true>(f, xd, p, &br);
-                const uint32_t n = (z * ny + y) * nx + x;
+            for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(in[src(i)], dev_ref<D, T>(i, p.dunit_f));
+            int br;
+            collide_stored<D, ST, true>(f, xd, p, &br);
+            const uint32_t n = (z * ny + y) * nx + x;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) out[uint32_t(i) * N + n] = step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f));
-            }
-            __syncthreads(); // every store of this segment issued
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(plan.cnt + seg.x, 1u);
-            }
+            for (int i = 0; i < Q; ++i) out[uint32_t(i) * N + n] = step_out<ST>(f[i], dev_ref<D, T>(i, p.dunit_f));
+        }
+        __syncthreads(); // every store of this chunk issued; s_ticket and s_ok read by all
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(plan.cnt + seg.x, 1u);
         }
     }
 }

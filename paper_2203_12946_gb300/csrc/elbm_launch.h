@@ -47,17 +47,18 @@ struct BatchTable {
     unsigned char coarse[kBatchCoarse];
 };
 
-// Static partition of one persistent ensemble launch (device arrays): block b
-// steps the work items of segments seg_off[b] .. seg_off[b+1]-1, each segment
-// {domain, first item, end item, 0} inside one domain (items numbered within the
-// domain); owners[d] blocks hold a segment of domain d, and cnt[d] counts their
-// finished (block, step) pairs.
+// Work of one persistent ensemble launch (device arrays): one step is cut into
+// nchunks chunks {domain, first item, end item, 0} (items numbered within the
+// domain), chunks[k] in domain order; owners[d] chunks belong to domain d, and cnt[d]
+// counts its finished (chunk, step) pairs.  Blocks draw tickets from *ticket in
+// order: ticket k is chunk k mod nchunks of step k / nchunks.
 struct PersistPlan {
     int grid = 0;
-    const int4 *segs = nullptr;
-    const int *seg_off = nullptr;
+    unsigned nchunks = 0;
+    const int4 *chunks = nullptr;
     const unsigned *owners = nullptr;
     unsigned *cnt = nullptr;
+    unsigned *ticket = nullptr;
 };
 
 // Device-side accumulator of the diagnostics reduction (library scratch).
