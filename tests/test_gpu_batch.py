@@ -219,3 +219,23 @@ def test_more_domains_than_one_launch_table(mode):
     for k, d in enumerate(dims):
         want, *_ = O.step(2, d, f0[k], betas[k], cutoff=False, nsteps=3)
         assert np.max(np.abs(got[k] - want) / want) < 1e-12, k
+
+
+@pytest.mark.parametrize("mode", [E.ELBM_BATCH_GRAPH, E.ELBM_BATCH_PERSISTENT, E.ELBM_BATCH_PER_DOMAIN])
+def test_fp32_two_node_kernels_on_ragged_domains(mode):
+    """D2Q9 FP32 domains collide two nodes per thread (x and x + 32 of a 64-node run);
+    sides that are not multiples of 32 leave threads whose second node, or both, lie past
+    the end of a row.  Each domain against the oracle over 5 steps, for the batched, the
+    persistent and the single-domain kernels."""
+    dims = [(33, 7, 1), (65, 12, 1), (97, 5, 1), (1, 9, 1), (31, 31, 1), (200, 3, 1), (129, 17, 1)]
+    betas = [0.99, 0.95, 0.999, 0.9, 0.97, 0.995, 0.93]
+    f0 = [domain_state(2, d, 2e-2, seed=400 + k).astype(np.float32) for k, d in enumerate(dims)]
+    with E.Ensemble(E.ELBM_D2Q9, dims, betas, storage="f32") as ens:
+        for k in range(len(dims)):
+            ens.set_populations(k, f0[k])
+        ens.step(5, mode)
+        got = [ens.get_populations(k).astype(np.float64) for k in range(len(dims))]
+        ens.synchronize()
+    for k, d in enumerate(dims):
+        want, *_ = O.step(2, d, f0[k].astype(np.float64), betas[k], nsteps=5)
+        assert np.max(np.abs(got[k] - want) / want) < 5 * 2e-6, k
