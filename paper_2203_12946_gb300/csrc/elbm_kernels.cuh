@@ -56,7 +56,9 @@ __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x
 // outweigh the spills, which fall in the per-population form of the coefficients
 // (large |x| only): 0.640 -> 0.627 ms per 256^3 step on GB300.  The 16-bit storages
 // lose with that cap (their loads and stores need more live values): 5 blocks, the
-// allocation they had unbounded.  FP64 (the parity path): no bound.
+// allocation they had unbounded.  FP32 deviations (d_i kept, f_i formed again at each
+// use): 6 blocks of 128 (80 registers; 0.6375 against 0.6574 ms early at 7).  FP64 (the
+// parity path): no bound.
 // ELBM_STEP_MIN_BLOCKS overrides.
 #ifndef ELBM_STEP_MIN_BLOCKS
 #define ELBM_STEP_MIN_BLOCKS 0
@@ -78,6 +80,7 @@ constexpr int step_min_blocks()
     return ELBM_STEP_MIN_BLOCKS > 0 ? ELBM_STEP_MIN_BLOCKS
                                     : (sizeof(typename ST::T) != 4 ? 1
                                        : D == 2 ? (ST::kDevCollide ? ELBM_PAIR_MIN_BLOCKS_DEV : ELBM_PAIR_MIN_BLOCKS)
+                                       : ST::kDevCollide          ? 6
                                        : sizeof(typename ST::S) == 4 ? 7 : 5);
 }
 // Two-node kernels: warp w of a block takes the aligned run of kPairSpan nodes
