@@ -39,6 +39,9 @@ struct elbm {
     int num_sms = 0;
     int64_t steps = 0;
     double force[3] = {0.0, 0.0, 0.0}; // uniform body force (elbm_set_force)
+    // load policy of the D3Q27 step (ld_pop): evict-first once the last diagnostics saw
+    // more than half of the nodes at |x|max >= 0.005 (the x^6 and per-population forms)
+    bool pop_stream = false;
     std::string err;
 };
 
@@ -86,6 +89,7 @@ CollideParams params_of(const elbm_t *h)
     p.beta_f = float(p.beta);
     p.dunit_f = h->D == 2 ? eelbm::dev_unit<2>(p.rho0) : eelbm::dev_unit<3>(p.rho0);
     for (int a = 0; a < 3; ++a) p.force[a] = h->force[a];
+    p.pop_stream = h->pop_stream ? 1 : 0;
     return p;
 }
 
@@ -340,6 +344,7 @@ int elbm_bind_buffers(elbm_t *h, void *pop_a, void *pop_b, size_t bytes)
     h->owned = false;
     h->cur = 0;
     h->steps = 0;
+    h->pop_stream = false; // a new state: the load policy waits for its diagnostics
     return ELBM_OK;
 }
 
@@ -394,6 +399,7 @@ int elbm_init_equilibrium(elbm_t *h, const double *rho, const double *u, int whe
     }
     h->cur = 0;
     h->steps = 0;
+    h->pop_stream = false; // a new state: the load policy waits for its diagnostics
     return ELBM_OK;
 }
 
@@ -549,6 +555,7 @@ int read_diag_acc(elbm_t *h, elbm_diag *out, int64_t *alpha_hist, const char *wh
     out->n_nonpositive = int64_t(acc.cnt[3]);
     out->n_dH_positive = int64_t(acc.cnt[4]);
     for (int b = 0; b < 4; ++b) out->n_xmax_band[b] = int64_t(acc.cnt[5 + b]);
+    h->pop_stream = 2 * (acc.cnt[7] + acc.cnt[8]) > uint64_t(N);
     if (alpha_hist)
         for (int b = 0; b < ELBM_HIST_BINS + 2; ++b) alpha_hist[b] = int64_t(acc.hist[b]);
     if (out->n_nonpositive > 0)
@@ -638,6 +645,7 @@ int elbm_set_populations(elbm_t *h, const void *src, int where)
     if (e != cudaSuccess) return cuda_fail(h, e, "elbm_set_populations");
     h->cur = 0;
     h->steps = 0;
+    h->pop_stream = false; // a new state: the load policy waits for its diagnostics
     return ELBM_OK;
 }
 

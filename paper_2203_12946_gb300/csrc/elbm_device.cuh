@@ -85,6 +85,7 @@ struct CollideParams {
     double force[3] = {0.0, 0.0, 0.0}; // uniform body force (not from the paper), used by the forced kernels
     float beta_f = 0.0f;  // beta rounded to FP32 once on the host (no FP64 conversion per thread)
     float dunit_f = 0.0f; // R = W rho0 rounded to FP32: the unit of the deviation references c_i = k_i R
+    int pop_stream = 0;   // host side: the D3Q27 step loads with the evict-first policy (ld_pop)
 };
 
 // beta in the compute type.
@@ -1199,6 +1200,20 @@ __device__ __forceinline__ void collide2_stored(typename ST::T (&fa)[Lattice<D>:
     int br;
     collide_stored<D, ST, kRelax>(fa, x, p, &br);
     collide_stored<D, ST, kRelax>(fb, x, p, &br);
+}
+
+// Population loads of the step kernels: through the read-only path (ld.global.nc), or,
+// with kStream, with the evict-first (streaming) policy (ld.global.cs): each line is read
+// once from DRAM and again, within a few warps, by the neighbours' shifted loads.  The
+// D3Q27 step takes the second where most nodes need the longer coefficient forms: there it
+// spills through L1, and population lines that leave L1 first keep room for the spills
+// (D3Q27 256^3 FP32, same box: 0.6807 against 0.6867 ms late in the benchmark flow, but
+// 0.5787 against 0.5727 early, where the step is bound by DRAM).
+template <bool kStream, class S>
+__device__ __forceinline__ S ld_pop(const S *p)
+{
+    if constexpr (kStream) return __ldcs(p);
+    else return __ldg(p);
 }
 
 // ---------------------------------------------------------------------------

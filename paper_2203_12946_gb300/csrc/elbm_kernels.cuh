@@ -31,6 +31,7 @@ constexpr int Q = Lattice<D>::Q;
 constexpr int kStepBlock = D == 2 ? 256 : ELBM_STEP_BLOCK_D3;
 constexpr int kAuxBlock = 256;
 
+
 __device__ __forceinline__ void node_coords(int64_t n, const Geometry &g, int &x, int &y, int &z)
 {
     if (g.N <= 0xffffffffll) { // 32-bit division where the indices fit (the common case)
@@ -97,7 +98,7 @@ constexpr int step_threads()
 }
 #define ELBM_STEP_BOUNDS __launch_bounds__(step_threads<ST>(), step_min_blocks<ST>())
 
-template <class ST, bool kGrid3D, bool kForce = false>
+template <class ST, bool kGrid3D, bool kForce = false, bool kStream = false>
 __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
                                                     typename ST::S *__restrict__ fout, Geometry g,
                                                     CollideParams p)
@@ -123,9 +124,9 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
                 return uint32_t(i) * N + sy * nx + sx;
             };
 #pragma unroll
-            for (int i = 0; i < Q; ++i) fa[i] = step_in<ST>(__ldg(fin + src(xa, i)), dev_ref<D, T>(i, p.dunit_f));
+            for (int i = 0; i < Q; ++i) fa[i] = step_in<ST>(ld_pop<false>(fin + src(xa, i)), dev_ref<D, T>(i, p.dunit_f));
 #pragma unroll
-            for (int i = 0; i < Q; ++i) fb[i] = step_in<ST>(__ldg(fin + src(xb, i)), dev_ref<D, T>(i, p.dunit_f));
+            for (int i = 0; i < Q; ++i) fb[i] = step_in<ST>(ld_pop<false>(fin + src(xb, i)), dev_ref<D, T>(i, p.dunit_f));
             collide2_stored<D, ST, true>(fa, fb, p);
             if constexpr (kForce) {
                 add_force<D, T, ST::kDevCollide>(fa, p);
@@ -187,7 +188,7 @@ __global__ void ELBM_STEP_BOUNDS k_step(const typename ST::S *__restrict__ fin,
             return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
         };
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(__ldg(fin + src(i)), dev_ref<D, T>(i, p.dunit_f));
+        for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(ld_pop<kStream>(fin + src(i)), dev_ref<D, T>(i, p.dunit_f));
         collide_stored<D, ST, true>(f, xd, p, &br);
         if constexpr (kForce) add_force<D, T, ST::kDevCollide>(f, p);
         const uint32_t n = (z * ny + y) * nx + x;
@@ -741,7 +742,7 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
         };
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = step_in<ST>(__ldg(fin + src(i)), dev_ref<D, T>(i, p.dunit_f));
+            f[i] = step_in<ST>(ld_pop<false>(fin + src(i)), dev_ref<D, T>(i, p.dunit_f));
             fc[i] = ST::kDevCollide ? f[i] + dev_ref<D, T>(i, p.dunit_f) : f[i]; // populations
         }
         int br;
@@ -757,7 +758,7 @@ __global__ void __launch_bounds__(kStepBlock, step_diag_min_blocks<ST>()) k_step
 // Two nodes x and x + 32 of row y of a D2Q9 domain (nx by ny, N nodes, populations
 // at in / out): pull, collide (node_collide_x2), store; a second node past the end of
 // the row is a copy of the first, collided and not stored.  Plain loads when kCoherent
-// (buffers written during the launch), else the read-only path.
+// (buffers written during the launch), else ld_pop.
 template <class ST, bool kCoherent = false>
 __device__ __forceinline__ void step2_row(const typename ST::S *in, typename ST::S *out, uint32_t nx, uint32_t ny,
                                           uint32_t N, uint32_t xa, uint32_t y, const CollideParams &p)
@@ -773,7 +774,7 @@ __device__ __forceinline__ void step2_row(const typename ST::S *in, typename ST:
         const uint32_t sy = cy == 1 ? ym : (cy == -1 ? yp : y);
         return uint32_t(i) * N + sy * nx + sx;
     };
-    auto ld = [&](uint32_t o) { return kCoherent ? in[o] : __ldg(in + o); };
+    auto ld = [&](uint32_t o) { return kCoherent ? in[o] : ld_pop<false>(in + o); };
     T fa[Q], fb[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) fa[i] = step_in<ST>(ld(src(xa, i)), dev_ref<D, T>(i, p.dunit_f));
@@ -864,7 +865,7 @@ __global__ void __launch_bounds__(BX / nodes_per_thread<D, ST>(), batch_min_bloc
         return uint32_t(i) * N + (sz * ny + sy) * nx + sx;
     };
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(__ldg(in + src(i)), dev_ref<D, T>(i, p.dunit_f));
+    for (int i = 0; i < Q; ++i) f[i] = step_in<ST>(ld_pop<false>(in + src(i)), dev_ref<D, T>(i, p.dunit_f));
     int br;
     collide_stored<D, ST, true>(f, xd, p, &br);
     const uint32_t n = (z * ny + y) * nx + x;
@@ -1235,6 +1236,14 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
     if (kernel == ELBM_KERNEL_ROWS) return cudaErrorNotSupported;
     if (g.ny <= 65535 && g.nz <= 65535 && uint64_t(Q) * uint64_t(g.N) <= 0xffffffffull) {
         const dim3 grid(unsigned((g.nx + kStepBlock - 1) / kStepBlock), unsigned(g.ny), unsigned(g.nz));
+        if constexpr (D == 3) {
+            if (!forced && p.pop_stream) {
+                ELBM_STORAGE_SWITCH(storage, (k_step<ST, true, false, true><<<grid, step_threads<ST>(), 0, s>>>(
+                                                 static_cast<const typename ST::S *>(fin),
+                                                 static_cast<typename ST::S *>(fout), g, p)));
+                return cudaGetLastError();
+            }
+        }
         if (forced) {
             ELBM_STORAGE_SWITCH(storage, (k_step<ST, true, true><<<grid, step_threads<ST>(), 0, s>>>(
                                              static_cast<const typename ST::S *>(fin),

@@ -278,6 +278,25 @@ def test_fp32_d2q9_two_node_collision_mixed_branches(storage, mode, b_variant):
     assert np.max(err[:, agree]) < 2e-6
 
 
+@pytest.mark.parametrize("storage", ["f32", "f32dev"])
+def test_load_policy_after_diagnostics_changes_no_result(storage):
+    """The D3Q27 step switches to evict-first population loads once the last diagnostics
+    saw most nodes on the longer coefficient forms; the arithmetic is the same, so the
+    populations after the steps are identical with and without that switch."""
+    D, dims, beta = 3, (40, 12, 9), 0.99
+    f0, _ = stored(D, noisy_state(D, dims, 3e-2, seed=71), storage)
+    outs = []
+    for diag_first in (False, True):
+        with E.Simulation(E.ELBM_D3Q27, dims, beta, storage=storage) as sim:
+            sim.set_populations(f0)
+            if diag_first:
+                d = sim.diagnostics()
+                assert d["n_xmax_band"][2] + d["n_xmax_band"][3] > d["n_nodes"] // 2
+            sim.step(3)
+            outs.append(sim.get_populations())
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("D,dims", [(2, (131, 29, 1)), (3, (21, 13, 9))])
 @pytest.mark.parametrize("storage", ["f32", "f32dev"])
 def test_fp32_iterate1_mode(D, dims, storage):
