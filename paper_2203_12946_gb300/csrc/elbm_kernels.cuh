@@ -1142,6 +1142,9 @@ static inline unsigned blocks_for(int64_t N, int block) { return unsigned((N + b
 #define ELBM_CAT2(a, b) a##_##b
 #define ELBM_CAT(a, b) ELBM_CAT2(a, b)
 
+// A lattice may be compiled in two units: ELBM_PART 1 holds the step launcher (and the
+// row pipeline), ELBM_PART 2 every other launcher; without ELBM_PART one unit holds all.
+#if !defined(ELBM_PART) || ELBM_PART == 1
 namespace ELBM_SUFFIX {
 
 // Row-staged instantiations: (NXMAX, stages) per storage element size.
@@ -1237,10 +1240,20 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
     if (g.ny <= 65535 && g.nz <= 65535 && uint64_t(Q) * uint64_t(g.N) <= 0xffffffffull) {
         const dim3 grid(unsigned((g.nx + kStepBlock - 1) / kStepBlock), unsigned(g.ny), unsigned(g.nz));
         if constexpr (D == 3) {
-            if (!forced && p.pop_stream) {
-                ELBM_STORAGE_SWITCH(storage, (k_step<ST, true, false, true><<<grid, step_threads<ST>(), 0, s>>>(
-                                                 static_cast<const typename ST::S *>(fin),
-                                                 static_cast<typename ST::S *>(fout), g, p)));
+            // the evict-first variant for the FP32-arithmetic storages (FP64, the parity
+            // path, keeps the read-only path)
+            if (!forced && p.pop_stream && storage != ELBM_STORE_F64) {
+#define ELBM_STREAM_STEP(STT)                                                                     \
+    k_step<STT, true, false, true><<<grid, step_threads<STT>(), 0, s>>>(                          \
+        static_cast<const typename STT::S *>(fin), static_cast<typename STT::S *>(fout), g, p)
+                switch (storage) {
+                case ELBM_STORE_F32: ELBM_STREAM_STEP(StoreF32); break;
+                case ELBM_STORE_F32DEV: ELBM_STREAM_STEP(StoreF32Dev); break;
+                case ELBM_STORE_F16DEV: ELBM_STREAM_STEP(StoreF16Dev); break;
+                case ELBM_STORE_BF16DEV: ELBM_STREAM_STEP(StoreBF16Dev); break;
+                default: return cudaErrorInvalidValue;
+                }
+#undef ELBM_STREAM_STEP
                 return cudaGetLastError();
             }
         }
@@ -1268,6 +1281,9 @@ cudaError_t ELBM_CAT(launch_step, ELBM_SUFFIX)(int storage, const void *fin, voi
     return cudaGetLastError();
 }
 
+#endif
+
+#if !defined(ELBM_PART) || ELBM_PART == 2
 cudaError_t ELBM_CAT(launch_step_diag, ELBM_SUFFIX)(int storage, const void *fin, void *fout, const Geometry &g,
                                                     const CollideParams &p, DiagAcc *acc, int num_sms,
                                                     cudaStream_t s)
@@ -1450,5 +1466,7 @@ cudaError_t ELBM_CAT(launch_diag, ELBM_SUFFIX)(int storage, const void *f, const
                                      static_cast<const typename ST::S *>(f), g, p, acc)));
     return cudaGetLastError();
 }
+
+#endif
 
 } // namespace eelbm
